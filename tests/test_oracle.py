@@ -1,0 +1,422 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a
+flipped sign, a swapped index or operand) fails at least one of them: closed
+forms of stencil Laplacians, identity and permutation matrices, dense brute
+force through numpy, scipy's CCS conversion, central finite differences, and
+the paper's printed table values.  ``test_planted_mistakes_are_caught`` plants
+such slips in a copy of the oracle source and checks that the pins notice.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+
+def grid_missing_2d(N):
+    """Number of 5-point neighbours of each grid point that fall outside the N x N grid."""
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    miss = (i == 0).astype(int) + (i == N - 1) + (j == 0) + (j == N - 1)
+    return miss.reshape(-1)
+
+
+def linear_2d_expected(N, a, b, c):
+    """(A x)_ij for x_ij = a i + b j + c under the Dirichlet 5-point Laplacian (diag 4, off -1):
+    the four differences x_ij - x_nbr cancel for a linear field, leaving the sum of the field's
+    values at the neighbours that lie outside the grid."""
+    out = np.zeros((N, N))
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        ii, jj = i + di, j + dj
+        outside = (ii < 0) | (ii >= N) | (jj < 0) | (jj >= N)
+        out += np.where(outside, a * ii + b * jj + c, 0.0)
+    return out.reshape(-1)
+
+
+def missing_3d(N):
+    """Number of 27-point neighbours (excluding the centre) outside the N^3 grid."""
+    idx = np.arange(N)
+    inside1 = np.array([1 + (x > 0) + (x < N - 1) for x in idx])  # neighbours along one axis incl. self
+    tot = inside1[:, None, None] * inside1[None, :, None] * inside1[None, None, :]
+    return (27 - tot).reshape(-1)
+
+
+def linear_3d_expected(N, a, b, c, d):
+    i, j, k = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    out = np.zeros((N, N, N))
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            for dk in (-1, 0, 1):
+                if di == dj == dk == 0:
+                    continue
+                ii, jj, kk = i + di, j + dj, k + dk
+                outside = (ii < 0) | (ii >= N) | (jj < 0) | (jj >= N) | (kk < 0) | (kk >= N)
+                out += np.where(outside, a * ii + b * jj + c * kk + d, 0.0)
+    return out.reshape(-1)
+
+
+def dense_ref(A: synth.CSR, X):
+    """Dense product through numpy, and the bound sum_p |val[p] X[col[p], :]| over the stored
+    nonzeros (duplicates count separately, as they are stored separately)."""
+    D = A.to_dense()
+    rows = np.repeat(np.arange(A.m), A.row_lengths())
+    Xa = np.asarray(X, dtype=np.float64)
+    prod = np.abs(A.vals.astype(np.float64)[:, None] * Xa.reshape(A.n, -1)[A.col_idx])
+    R = np.zeros((A.m, prod.shape[1]))
+    np.add.at(R, rows, prod)
+    return D @ Xa, R.reshape((A.m,) + Xa.shape[1:])
+
+
+# ------------------------------------------------------- generator pins
+
+def test_stencil2d_counts_and_paper_mesh_2048():
+    for N in (1, 2, 3, 7, 64):
+        A = synth.stencil2d(N)
+        assert A.nnz == 5 * N * N - 4 * N
+        assert A.row_ptr[0] == 0 and A.row_ptr[-1] == A.nnz
+    assert synth.stencil2d(64).nnz == 20224
+    # Paper Table "tab:matrices" row 20: mesh_2048
+    fields = None
+    for line in open(os.path.join(GOLDEN, "mesh_2048.txt")):
+        if line.startswith("mesh_2048"):
+            fields = line.split()
+    rows, nnz, maxr = int(fields[1]), int(fields[2]), int(fields[4])
+    A = synth.stencil2d(2048)
+    assert A.m == rows and A.nnz == nnz
+    assert A.row_lengths().max() == maxr
+    # the table prints nnz/row truncated to two decimals (20963328 / 4194304 = 4.998...)
+    assert int(A.nnz / A.m * 100) / 100 == float(fields[3])
+
+
+def test_stencil3d_counts():
+    for N in (1, 2, 3, 5):
+        A = synth.stencil3d(N)
+        assert A.nnz == (3 * N - 2) ** 3
+    assert (3 * 100 - 2) ** 3 == 26463592
+
+
+def test_generators_structure():
+    B = synth.banded(5000, hbw=100, per_row=20, seed=7)
+    lens = B.row_lengths()
+    assert (lens == 20).all()
+    for i in (0, 1, 2500, 4999):
+        cols = B.col_idx[B.row_ptr[i]:B.row_ptr[i + 1]]
+        assert (np.diff(cols) > 0).all() and i in cols
+        assert np.abs(cols - i).max() <= 100
+        v = B.vals[B.row_ptr[i]:B.row_ptr[i + 1]]
+        diag = v[cols == i][0]
+        assert diag == pytest.approx(np.abs(v[cols != i]).sum() + 1.0, rel=1e-15)
+    R = synth.rmat(12, ef=8, seed=3)
+    assert R.nnz <= 8 * 4096 and R.nnz > 4096
+    rows = np.repeat(np.arange(R.m), R.row_lengths())
+    key = rows.astype(np.int64) * R.n + R.col_idx
+    assert (np.diff(key) > 0).all()  # sorted and deduplicated
+    # determinism
+    R2 = synth.rmat(12, ef=8, seed=3)
+    assert np.array_equal(R.col_idx, R2.col_idx) and np.array_equal(R.row_ptr, R2.row_ptr)
+    u = synth.uniform(1000, -1, 1, seed=5)
+    assert u.min() >= -1 and u.max() < 1 and abs(u.mean()) < 0.1
+
+
+# ------------------------------------------------------------ SpMV pins
+
+def check_spmv_closed_forms(spmv):
+    """Closed-form pins of an SpMV callable spmv(m, rp, ci, v, x) -> (y, r)."""
+    for N in (1, 2, 5, 16):
+        A = synth.stencil2d(N)
+        y, r = spmv(A.m, A.row_ptr, A.col_idx, A.vals, np.ones(A.n))
+        assert np.array_equal(y, grid_missing_2d(N).astype(float)), "A*1 on the 2D Laplacian"
+        assert np.array_equal(r, (4.0 + (4 - grid_missing_2d(N))).astype(float)), "sum |a x| on A*1"
+        a, b, c = 0.75, -1.25, 0.5
+        i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+        x = (a * i + b * j + c).reshape(-1).astype(float)
+        y, _ = spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+        assert np.allclose(y, linear_2d_expected(N, a, b, c), rtol=0, atol=1e-12), "2D linear field"
+    for N in (2, 4):
+        A = synth.stencil3d(N)
+        y, _ = spmv(A.m, A.row_ptr, A.col_idx, A.vals, np.ones(A.n))
+        assert np.array_equal(y, missing_3d(N).astype(float)), "A*1 on the 27-point stencil"
+        i, j, k = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+        x = (0.5 * i - 0.25 * j + 2.0 * k + 1.0).reshape(-1)
+        y, _ = spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+        assert np.allclose(y, linear_3d_expected(N, 0.5, -0.25, 2.0, 1.0), rtol=0, atol=1e-12), "3D linear"
+
+
+def check_spmv_permutation(spmv):
+    rng = np.random.default_rng(11)
+    for m in (1, 7, 100):
+        # identity
+        rp = np.arange(m + 1, dtype=np.int32)
+        ci = np.arange(m, dtype=np.int32)
+        x = rng.uniform(-1, 1, m)
+        y, _ = spmv(m, rp, ci, np.ones(m), x)
+        assert np.array_equal(y, x), "identity"
+        # permutation: row i holds a single 1 in column pi[i], so y_i = x[pi[i]]
+        pi = rng.permutation(m).astype(np.int32)
+        y, _ = spmv(m, rp, pi, np.ones(m), x)
+        assert np.array_equal(y, x[pi]), "permutation"
+        # scaled permutation
+        s = rng.uniform(0.5, 2.0, m)
+        y, _ = spmv(m, rp, pi, s, x)
+        assert np.array_equal(y, s * x[pi])
+
+
+def check_spmv_brute_force(spmv):
+    cases = [
+        synth.random_csr(1, 1, 1.0, 1),
+        synth.random_csr(5, 9, 0.4, 2, empty_rows=0.3),
+        synth.random_csr(40, 17, 0.3, 3),
+        synth.random_csr(17, 40, 0.3, 4, empty_rows=0.2),
+        synth.random_csr(64, 64, 0.1, 5, sorted_cols=False),
+        synth.random_csr(30, 30, 0.2, 6, duplicates=True),
+        synth.random_csr(20, 20, 0.0, 7),  # tau = 0
+    ]
+    # one full row among empty ones
+    rp = np.zeros(9, np.int32)
+    rp[4:] = 33
+    cases.append(synth.CSR(8, 33, rp, np.arange(33, dtype=np.int32), np.linspace(-1, 1, 33)))
+    rng = np.random.default_rng(12)
+    for A in cases:
+        x = rng.uniform(-1, 1, A.n)
+        y, r = spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+        yd, rd = dense_ref(A, x)
+        assert y.shape == (A.m,)
+        assert np.all(np.abs(y - yd) <= 1e-14 * rd + 0.0), "dense brute force"
+        assert np.allclose(r, rd, rtol=1e-14, atol=0)
+        assert np.all(np.abs(y) <= r * (1 + 1e-15))
+        empty = A.row_lengths() == 0
+        assert np.all(y[empty] == 0.0) and np.all(r[empty] == 0.0)
+
+
+def _oracle_spmv(m, rp, ci, v, x):
+    return oracle.spmv(m, rp, ci, v, x)
+
+
+def test_spmv_closed_forms():
+    check_spmv_closed_forms(_oracle_spmv)
+
+
+def test_spmv_identity_permutation():
+    check_spmv_permutation(_oracle_spmv)
+
+
+def test_spmv_dense_brute_force():
+    check_spmv_brute_force(_oracle_spmv)
+
+
+def test_spmv_threads_do_not_change_result():
+    A = synth.banded(3000, hbw=50, per_row=12, seed=9)
+    x = synth.uniform(A.n, seed=9)
+    y1, r1 = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x, threads=1)
+    y4, r4 = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x, threads=4)
+    assert np.array_equal(y1, y4) and np.array_equal(r1, r4)
+
+
+def test_spmv_f32_inputs_accumulate_in_f64():
+    rng = np.random.default_rng(13)
+    A = synth.random_csr(50, 70, 0.3, 14, empty_rows=0.1)
+    v32 = A.vals.astype(np.float32)
+    x32 = rng.uniform(-1, 1, A.n).astype(np.float32)
+    y, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, v32, x32)
+    D = synth.CSR(A.m, A.n, A.row_ptr, A.col_idx, v32.astype(np.float64)).to_dense()
+    yd = D @ x32.astype(np.float64)
+    rd = np.abs(D) @ np.abs(x32.astype(np.float64))
+    # float x float products are exact in double; only the double sums round
+    assert np.all(np.abs(y - yd) <= 1e-14 * rd)
+    assert y.dtype == np.float64
+
+
+# ------------------------------------------------------------ SpMM pins
+
+def test_spmm_dense_brute_force_and_columns():
+    rng = np.random.default_rng(21)
+    for (m, n, k, dens, seed) in ((9, 13, 1, 0.3, 1), (40, 25, 4, 0.2, 2), (25, 40, 8, 0.15, 3),
+                                  (64, 64, 16, 0.1, 4), (10, 10, 3, 0.0, 5), (33, 31, 5, 0.25, 6)):
+        A = synth.random_csr(m, n, dens, seed, empty_rows=0.2)
+        wide = rng.uniform(-1, 1, (n, k + 3))
+        X = wide[:, :k]  # leading dimension k + 3 > k
+        Y, R = oracle.spmm(m, A.row_ptr, A.col_idx, A.vals, X)
+        Yd, Rd = dense_ref(A, X)
+        assert Y.shape == (m, k)
+        assert np.all(np.abs(Y - Yd) <= 1e-14 * Rd)
+        assert np.allclose(R, Rd, rtol=1e-14, atol=0)
+        for c in range(k):  # column c of Y is the SpMV of column c of X
+            yc, _ = oracle.spmv(m, A.row_ptr, A.col_idx, A.vals, np.ascontiguousarray(X[:, c]))
+            assert np.array_equal(Y[:, c], yc)
+
+
+def test_spmm_stencil_constant_columns():
+    N = 8
+    A = synth.stencil2d(N)
+    X = np.stack([np.ones(A.n), 2 * np.ones(A.n), -np.ones(A.n)], axis=1)
+    Y, _ = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals, X)
+    miss = grid_missing_2d(N).astype(float)
+    assert np.array_equal(Y[:, 0], miss) and np.array_equal(Y[:, 1], 2 * miss) and np.array_equal(Y[:, 2], -miss)
+
+
+# ------------------------------------------------------- transpose pins
+
+def test_transpose_matches_scipy_and_is_involution():
+    sp = pytest.importorskip("scipy.sparse")
+    for (m, n, dens, seed) in ((1, 1, 1.0, 1), (13, 29, 0.3, 2), (29, 13, 0.3, 3), (64, 64, 0.05, 4), (7, 7, 0.0, 5)):
+        A = synth.random_csr(m, n, dens, seed, empty_rows=0.2)
+        marker = np.arange(A.nnz, dtype=np.float64) + 1.0  # identifies each nonzero
+        S = sp.csr_matrix((marker, A.col_idx, A.row_ptr), shape=(m, n))
+        C = S.tocsc()  # the dual CCS of A is the CRS of A^T (Sec. 3)
+        rpT, ciT, perm = oracle.transpose(m, n, A.row_ptr, A.col_idx)
+        assert np.array_equal(rpT, C.indptr) and np.array_equal(ciT, C.indices)
+        assert np.array_equal(perm.astype(np.float64) + 1.0, C.data)
+        rpTT, ciTT, permTT = oracle.transpose(n, m, rpT, ciT)
+        assert np.array_equal(rpTT, A.row_ptr) and np.array_equal(ciTT, A.col_idx)
+        assert np.array_equal(perm[permTT], np.arange(A.nnz))
+
+
+def test_transpose_stability_with_duplicates_and_unsorted():
+    A = synth.random_csr(30, 12, 0.3, 8, sorted_cols=False, duplicates=True)
+    rpT, ciT, perm = oracle.transpose(A.m, A.n, A.row_ptr, A.col_idx)
+    rows = np.repeat(np.arange(A.m), A.row_lengths())
+    # brute force: column j of A, in order of storage
+    for j in range(A.n):
+        expect = [p for p in range(A.nnz) if A.col_idx[p] == j]
+        got = perm[rpT[j]:rpT[j + 1]]
+        assert list(got) == expect
+        assert np.array_equal(ciT[rpT[j]:rpT[j + 1]], rows[expect])
+
+
+def test_transpose_rejects_bad_column():
+    rp = np.array([0, 2], np.int32)
+    with pytest.raises(ValueError):
+        oracle.transpose(1, 3, rp, np.array([0, 3], np.int32))
+
+
+def test_adjoint_identity():
+    rng = np.random.default_rng(31)
+    A = synth.random_csr(50, 35, 0.2, 9)
+    x, w = rng.uniform(-1, 1, A.n), rng.uniform(-1, 1, A.m)
+    rpT, ciT, perm = oracle.transpose(A.m, A.n, A.row_ptr, A.col_idx)
+    Ax, _ = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+    ATw, _ = oracle.spmv(A.n, rpT, ciT, A.vals[perm], w)
+    assert abs(Ax @ w - x @ ATw) <= 1e-13 * (np.abs(A.vals).sum() + 1)
+
+
+# -------------------------------------------------------- backward pins
+
+def _loss(A, vals, X, W):
+    """L = <A X, W> computed densely in numpy (independent of the oracle)."""
+    D = synth.CSR(A.m, A.n, A.row_ptr, A.col_idx, vals).to_dense()
+    return float(np.sum((D @ X) * W))
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_backward_finite_differences(k):
+    rng = np.random.default_rng(40 + k)
+    A = synth.random_csr(23, 19, 0.25, 41 + k, empty_rows=0.1, duplicates=True)
+    X = rng.uniform(-1, 1, (A.n, k))
+    W = rng.uniform(-1, 1, (A.m, k))
+    dX, dvals, RdX, Rdv = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, A.vals, X, W)
+    h = 1e-6
+    # L is bilinear in (vals, X): a central difference is exact up to rounding
+    for _ in range(8):
+        dv = rng.uniform(-1, 1, A.nnz)
+        fd = (_loss(A, A.vals + h * dv, X, W) - _loss(A, A.vals - h * dv, X, W)) / (2 * h)
+        assert fd == pytest.approx(dvals @ dv, rel=1e-7, abs=1e-9)
+        dx = rng.uniform(-1, 1, X.shape)
+        fd = (_loss(A, A.vals, X + h * dx, W) - _loss(A, A.vals, X - h * dx, W)) / (2 * h)
+        assert fd == pytest.approx(np.sum(dX * dx), rel=1e-7, abs=1e-9)
+    # dense brute force
+    D = A.to_dense()
+    assert np.allclose(dX, D.T @ W, rtol=1e-13, atol=1e-13)
+    rows = np.repeat(np.arange(A.m), A.row_lengths())
+    assert np.allclose(dvals, np.einsum("pc,pc->p", W[rows], X[A.col_idx]), rtol=1e-13, atol=1e-14)
+    RdX_bf = np.zeros_like(RdX)
+    np.add.at(RdX_bf, A.col_idx, np.abs(A.vals[:, None] * W[rows]))
+    assert np.allclose(RdX, RdX_bf, rtol=1e-13)
+    assert np.all(Rdv >= np.abs(dvals) - 1e-15)
+
+
+def test_backward_f32_inputs():
+    rng = np.random.default_rng(50)
+    A = synth.random_csr(20, 30, 0.3, 51).astype(np.float32)
+    X = rng.uniform(-1, 1, (A.n, 4)).astype(np.float32)
+    W = rng.uniform(-1, 1, (A.m, 4)).astype(np.float32)
+    dX, dvals, _, _ = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, A.vals, X, W)
+    D = synth.CSR(A.m, A.n, A.row_ptr, A.col_idx, A.vals.astype(np.float64)).to_dense()
+    assert np.allclose(dX, D.T @ W.astype(np.float64), rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------- batch offsets
+
+def test_batch_offsets_brute_force():
+    rng = np.random.default_rng(60)
+    ms = rng.integers(0, 1000, 37).astype(np.int32)
+    ns = rng.integers(1, 1000, 37).astype(np.int32)
+    nnz = rng.integers(0, 10**6, 37).astype(np.int64)
+    k = 8
+    off_rows, off_nnz, off_rp, off_x, off_y = oracle.batch_offsets(ms, ns, nnz, k)
+    r = z = rp = xo = yo = 0
+    for b in range(37):
+        assert (off_rows[b], off_nnz[b], off_rp[b], off_x[b], off_y[b]) == (r, z, rp, xo, yo)
+        r += int(ms[b]); z += int(nnz[b]); rp += int(ms[b]) + 1; xo += int(ns[b]) * k; yo += int(ms[b]) * k
+    assert (off_rows[37], off_nnz[37], off_rp[37], off_x[37], off_y[37]) == (r, z, rp, xo, yo)
+
+
+# ---------------------------------------------- planted mistakes (mutation)
+
+MUTATIONS = [
+    # (name, text in oracle.c, replacement); every replacement stays in bounds
+    ("dropped last term", "for (int p = rptrs[i]; p < rptrs[i + 1]; ++p) {\n      double t = val[p] * x[cids[p]];",
+     "for (int p = rptrs[i]; p + 1 < rptrs[i + 1]; ++p) {\n      double t = val[p] * x[cids[p]];"),
+    ("dropped first term", "for (int p = rptrs[i]; p < rptrs[i + 1]; ++p) {\n      double t = val[p] * x[cids[p]];",
+     "for (int p = rptrs[i] + 1; p < rptrs[i + 1]; ++p) {\n      double t = val[p] * x[cids[p]];"),
+    ("wrong sign", "s = s + t;", "s = s - t;"),
+    ("wrong x index", "double t = val[p] * x[cids[p]];", "double t = val[p] * x[cids[rptrs[i]]];"),
+    ("wrong value index", "double t = val[p] * x[cids[p]];", "double t = val[rptrs[i]] * x[cids[p]];"),
+    ("abs bound without abs", "a = a + fabs(t);", "a = a + t;"),
+]
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert old in src
+    mutated = src.replace(old, new, 1)
+    c = tmp_path / "mut.c"
+    c.write_text(mutated)
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.orc_spmv_f64.argtypes = [i32, P, P, P, P, P, P, i32]
+
+    def spmv(m, rp, ci, v, x):
+        rp = np.ascontiguousarray(rp, np.int32)
+        ci = np.ascontiguousarray(ci, np.int32)
+        v = np.ascontiguousarray(v, np.float64)
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.empty(m)
+        r = np.empty(m)
+        lib.orc_spmv_f64(m, rp.ctypes.data, ci.ctypes.data if ci.size else 0, v.ctypes.data if v.size else 0,
+                         x.ctypes.data, y.ctypes.data, r.ctypes.data, 1)
+        return y, r
+
+    return spmv
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistakes_are_caught(tmp_path, name, old, new):
+    spmv = _build_mutant(tmp_path, old, new)
+    caught = 0
+    for check in (check_spmv_closed_forms, check_spmv_permutation, check_spmv_brute_force):
+        try:
+            check(spmv)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, f"no pin caught the planted mistake: {name}"
