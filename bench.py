@@ -1,0 +1,438 @@
+"""Benchmark of the CSR SpMV / SpMM hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload spmv|spmm|small] [--impl reference]
+
+Default workload (one "step" = one pass over all of it): FP64 SpMV y <- A x
+(paper Sec. 3) on three synthetic matrices shaped like the paper's test set
+(Sec. 4, Table "tab:matrices"): a 3D 27-point stencil on 100^3 (regular mesh
+class), a random banded FEM-like matrix with 2M rows and 50 nonzeros per row
+(FEM class), and an R-MAT graph of scale 22, edge factor 16 (power-law
+class).  Each matrix runs through an autotuned plan.  Inputs are resident in
+HBM when timing starts; the L2 is flushed (a 256 MiB write, not timed)
+before every step, and every matrix is larger than the L2 anyway.
+
+Reported (one JSON line on rank 0): GFLOP/s = 2 * nnz * k / t over all
+ranks, the per-launch roofline of the dominant kernel against the measured
+HBM copy bandwidth (compulsory bytes, Sec. 4.2: 12 nnz + 4 (m+1) + 8 n k +
+8 m k) and against the FP64 FMA rate measured live (GB300's second roof),
+an end-to-end figure through the public API with host buffers, the CPU
+oracle timed on the host cores, and the SM clocks sampled during timing.
+
+--gpus N > 1 runs under torchrun: every rank multiplies its own independent
+matrices (weak scaling, no collective on the data path; one all-reduce of
+the timings).  --impl reference times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "CSR SpMV/SpMM GFLOP/s & % of HBM roofline at FP64; batched vs looped"
+UNIT = "GFLOP/s"
+
+
+# ------------------------------------------------------------------ workloads
+
+def workload_matrices(name: str, rank: int):
+    """(name, CSR, k list) of a workload; rank shifts the seeds so ranks hold independent problems."""
+    s = synth.BASE_SEED + 1 + 1000 * rank
+    if name == "small":
+        return [("stencil2d_64", synth.stencil2d(64))], [1]
+    if name in ("spmv", "spmm"):
+        mats = [("stencil3d_100", synth.stencil3d(100)),
+                ("banded_2M_hbw1000_50", synth.banded(2_000_000, hbw=1000, per_row=50, seed=s)),
+                ("rmat_s22_ef16", synth.rmat(22, ef=16, seed=s))]
+        return mats, ([1] if name == "spmv" else [1, 4, 8, 16])
+    raise ValueError(name)
+
+
+WORKLOAD_TEXT = {
+    "spmv": "FP64 CSR SpMV sweep: 3D 27-pt stencil 100^3 (m=1,000,000, nnz=26,463,592); random banded "
+            "m=2,000,000 hbw 1000 50 nnz/row N(0,1) dominant diagonal; R-MAT scale 22 ef 16 "
+            "(a,b,c=0.57,0.19,0.19) dedup, vals 1.0; x uniform[-1,1]",
+    "spmm": "FP64 CSR SpMM Y=A X, X row-major n x k, k in {1,4,8,16}, on the 27-pt 100^3, banded 2M and "
+            "R-MAT 22 matrices; X uniform[-1,1]",
+    "small": "FP64 CSR SpMV, 2D 5-pt Laplacian 64x64 (m=4096, nnz=20,224)",
+}
+
+
+def compulsory_bytes(m, n, nnz, k, es=8):
+    """Sec. 4.2 / Sec. 5 application-bandwidth model with (m+1) row pointers:
+    es*nnz + 4*nnz + 4*(m+1) + es*n*k + es*m*k."""
+    return (es + 4) * nnz + 4 * (m + 1) + es * n * k + es * m * k
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 4 + i and r[4 + i].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev_index: int) -> str:
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        return ids[dev_index] if dev_index < len(ids) else str(dev_index)
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(mats, ks, budget_s: float = 12.0, frac_rows: float | None = None):
+    """Time the CPU oracle (paper Sec. 4.1 row-parallel loop, all host cores) on the workload's
+    matrices, repeating whole sweeps until `budget_s` is spent (at least one sweep, over a
+    leading fraction of the rows if `frac_rows` is given).  Returns (GFLOP/s, cores, text)."""
+    import oracle
+
+    threads = oracle.max_threads()
+    xs = {}
+    flops = 0.0
+    t_total = 0.0
+    sweeps = 0
+    while True:
+        for name, A in mats:
+            r1 = A.m if frac_rows is None else max(1, int(A.m * frac_rows))
+            rp = A.row_ptr[: r1 + 1]
+            nz = int(rp[-1])
+            for k in ks:
+                key = (name, k)
+                if key not in xs:
+                    xs[key] = synth.uniform(A.n * k, seed=7, stream=k).reshape(A.n, k) if k > 1 else \
+                        synth.uniform(A.n, seed=7)
+                t0 = time.perf_counter()
+                if k == 1:
+                    oracle.spmv(r1, rp, A.col_idx, A.vals, xs[key], threads=threads)
+                else:
+                    oracle.spmm(r1, rp, A.col_idx, A.vals, xs[key], threads=threads)
+                t_total += time.perf_counter() - t0
+                flops += 2.0 * nz * k
+        sweeps += 1
+        if t_total >= budget_s or sweeps >= 50:
+            break
+    what = f"{sweeps} full sweep(s)" if frac_rows is None else f"{sweeps} sweep(s) over the first {frac_rows:.0%} of rows"
+    return flops / t_total / 1e9, threads, f"{what} of the workload, {t_total:.1f} s of CPU time"
+
+
+# --------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    mats, ks = workload_matrices(args.workload, 0)
+    import oracle
+
+    threads = oracle.max_threads()
+    # size each step so that warmup + steps stays within about two minutes
+    total_nnz = sum(A.nnz for _, A in mats) * len(ks)
+    est_step = total_nnz * 2e-9 * 8 / max(1, threads)  # rough seconds per full sweep
+    nsteps = args.steps + args.warmup
+    frac = None
+    if est_step * nsteps > 120:
+        frac = max(0.001, 120 / (est_step * nsteps))
+    times, flops = [], []
+    xs = {}
+    for step in range(nsteps):
+        f = 0.0
+        t0 = time.perf_counter()
+        for name, A in mats:
+            r1 = A.m if frac is None else max(1, int(A.m * frac))
+            rp = A.row_ptr[: r1 + 1]
+            for k in ks:
+                key = (name, k)
+                if key not in xs:
+                    xs[key] = synth.uniform(A.n * k, seed=7, stream=k).reshape(A.n, k) if k > 1 else \
+                        synth.uniform(A.n, seed=7)
+                if k == 1:
+                    oracle.spmv(r1, rp, A.col_idx, A.vals, xs[key], threads=threads)
+                else:
+                    oracle.spmm(r1, rp, A.col_idx, A.vals, xs[key], threads=threads)
+                f += 2.0 * int(rp[-1]) * k
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            flops.append(f)
+    value = sum(flops) / sum(times) / 1e9
+    sample = "whole workload per step" if frac is None else f"first {frac:.1%} of the rows of each matrix per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"CPU oracle (row-parallel OpenMP, dynamic,64), {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def launches_per_call(cfg: dict, k: int, dtype_vec: int = 2) -> int:
+    """Kernels one product call launches: ROWS 1 per column panel; MERGE partition is
+    precomputed by the plan, then kernel + carry fix-up per panel."""
+    panel = 32 * dtype_vec if k > 1 else 1
+    panels = (k + panel - 1) // panel
+    return panels * (1 if cfg["variant"] == 1 else 2)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    gbs.lib()
+
+    mats, ks = workload_matrices(args.workload, rank)
+    # ---- resident inputs and tuned plans
+    items = []
+    for name, A in mats:
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col_idx).to(dev)
+        v = torch.from_numpy(A.vals).to(dev)
+        for k in ks:
+            X = synth.uniform(A.n * k, seed=synth.BASE_SEED + 11 + rank, stream=k)
+            Xd = torch.from_numpy(X).to(dev).reshape(A.n, k) if k > 1 else torch.from_numpy(X).to(dev)
+            Yd = torch.empty((A.m, k) if k > 1 else (A.m,), dtype=torch.float64, device=dev)
+            plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True)
+            items.append(dict(name=name, A=A, k=k, rp=rp, ci=ci, v=v, X=Xd, Y=Yd, plan=plan, cfg=plan.config,
+                              bytes=compulsory_bytes(A.m, A.n, A.nnz, k), flops=2.0 * A.nnz * k))
+    stream = torch.cuda.current_stream(dev)
+
+    def call(it):
+        if it["k"] == 1:
+            it["plan"].spmv(it["v"], it["X"], it["Y"])
+        else:
+            it["plan"].spmm(it["v"], it["X"], it["Y"])
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # ---- FP64 FMA rate (second roof), measured live
+    probe_out = torch.empty(152 * 8 * 256, dtype=torch.float64, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads_p, iters = sms * 8, 256, 2048
+    L = gbs.lib()
+    for _ in range(2):
+        L.gbs_fp64_probe(probe_out.data_ptr(), blocks, threads_p, iters, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.gbs_fp64_probe(probe_out.data_ptr(), blocks, threads_p, iters, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_peak_gflops = 2.0 * 8 * iters * blocks * threads_p / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        for it in items:
+            call(it)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps; per-launch events on the launching stream
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+          for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_smi_id(torch, local_rank))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.05)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        for j, it in enumerate(items):
+            ev[s][j][0].record(stream)
+            call(it)
+            ev[s][j][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    sampler.stop()
+    per_item_ms = [[ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(args.steps)] for j in range(len(items))]
+    step_ms = sum(statistics.mean(t) for t in per_item_ms)
+    flops_step = sum(it["flops"] for it in items)
+
+    # ---- end to end through the public API with host buffers (H2D inputs, D2H result, each step)
+    pinned = []
+    for it in items:
+        A = it["A"]
+        hb = dict(rp=torch.from_numpy(A.row_ptr).pin_memory(), ci=torch.from_numpy(A.col_idx).pin_memory(),
+                  v=torch.from_numpy(A.vals).pin_memory(), X=it["X"].cpu().pin_memory(),
+                  Y=torch.empty(it["Y"].shape, dtype=torch.float64).pin_memory())
+        pinned.append(hb)
+    h2d = sum(h["rp"].numel() * 4 + h["ci"].numel() * 4 + h["v"].numel() * 8 + h["X"].numel() * 8 for h in pinned)
+    d2h = sum(h["Y"].numel() * 8 for h in pinned)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record(stream)
+    for _ in range(e2e_steps):
+        for it, hb in zip(items, pinned):
+            it["rp"].copy_(hb["rp"], non_blocking=True)
+            it["ci"].copy_(hb["ci"], non_blocking=True)
+            it["v"].copy_(hb["v"], non_blocking=True)
+            it["X"].copy_(hb["X"], non_blocking=True)
+            call(it)
+            hb["Y"].copy_(it["Y"], non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
+
+    # ---- max over ranks
+    t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max, e2e_ms_max = float(t[0]), float(t[1])
+
+    # ---- per-matrix report, dominant kernel roofline
+    hbm_peak = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
+    peak_src = "measured"
+    if not hbm_peak:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    per = []
+    for j, it in enumerate(items):
+        ms = statistics.mean(per_item_ms[j])
+        per.append({"matrix": it["name"], "k": it["k"], "m": it["A"].m, "nnz": it["A"].nnz, "config": it["cfg"],
+                    "ms": ms, "gflops": it["flops"] / ms / 1e6, "hbm_gbs": it["bytes"] / ms / 1e6,
+                    "hbm_frac": it["bytes"] / ms / 1e6 / hbm_peak,
+                    "fp64_frac": it["flops"] / ms / 1e6 / fp64_peak_gflops})
+    dom = max(range(len(items)), key=lambda j: per[j]["ms"])
+    d = per[dom]
+    t_hbm = items[dom]["bytes"] / (hbm_peak * 1e9)
+    t_alu = items[dom]["flops"] / (fp64_peak_gflops * 1e9)
+    hbm_roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": d["hbm_frac"],
+                "traffic": None, "kernel": f"{d['matrix']} k={d['k']} {d['config']}",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"}
+    alu_roof = {"bound": "alu", "achieved": d["gflops"], "peak": fp64_peak_gflops, "unit": "GFLOP/s",
+                "frac": d["fp64_frac"], "peak_source": "FP64 FMA rate measured live in this run (gbs_fp64_probe)"}
+    roofline = hbm_roof
+    roofline["binding_roof"] = "fp64_alu" if t_alu > t_hbm else "hbm"
+    roofline["fp64_alu"] = alu_roof
+
+    launches = args.steps * sum(launches_per_call(it["cfg"], it["k"]) for it in items)
+    line = {
+        "metric": METRIC, "value": world * flops_step / (step_ms_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "parallelism": f"independent problems per GPU x{world}",
+                   "l2": "256 MiB write before every step (untimed); every matrix exceeds the L2",
+                   "timing": "CUDA events around each product on the launching stream; value uses their sum",
+                   "wall_s_timed_region": wall},
+        "roofline": roofline,
+        "e2e": {"value": world * flops_step / (e2e_ms_max * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "clocks": sampler.summary(),
+        "gpu_launches": launches,
+        "fp64_fma_peak_gflops": fp64_peak_gflops,
+        "per_matrix": per,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, what = cpu_oracle_rate(mats, ks)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": what}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small"])
+    ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and "WORLD_SIZE" not in os.environ:
+        world = 1
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

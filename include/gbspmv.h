@@ -1,0 +1,194 @@
+/*
+ * gbspmv — CSR sparse-matrix products on NVIDIA GB300 (sm_103a), C ABI.
+ *
+ * Operations (Saule, Kaya, Catalyurek, "Performance Evaluation of Sparse
+ * Matrix Multiplication Kernels on Intel Xeon Phi", arXiv:1302.1078):
+ *
+ *   SpMV  y <- A x       (Sec. 1, Sec. 3): A is m x n, x has n entries,
+ *                        y has m entries; y_i is the dot product of row i of
+ *                        A with x (2 * nnz flops).
+ *   SpMM  Y <- A X       (Sec. 3, Sec. 5): X is n x k and Y is m x k, both
+ *                        row major, so that each nonzero (i, j) reads the
+ *                        contiguous row X[j, :] (2 * nnz * k flops).
+ *
+ * A is given in the compressed-row storage of Sec. 3: row_ptr[m+1] with
+ * row_ptr[0] = 0 and row_ptr[m] = nnz; the nonzeros of row i are stored at
+ * positions row_ptr[i] .. row_ptr[i+1]-1 of col_idx[nnz] (column ids) and
+ * vals[nnz] (values).  Indices are 32-bit (Sec. 4).  Values are double
+ * (the paper's precision, Sec. 4) or float.  Columns inside a row may be
+ * unsorted or repeated; repeated entries add up.
+ *
+ * Beyond the paper: the backward pass of Y = A X (dX = A^T dY and dvals, the
+ * gradient of a loss with respect to the stored values), a deterministic CSR
+ * transpose, and a batched mode that multiplies many matrices in one
+ * persistent launch replayed from a CUDA graph.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless the
+ *     argument says "host".  The library never frees them and keeps no
+ *     reference to them after the call returns, except where a plan says so.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - y / Y / dX / dvals are overwritten, never read (no alpha/beta).  An
+ *     empty row yields 0.
+ *   - Results are bitwise reproducible from run to run: no floating-point
+ *     atomics are used and every summation order is fixed.
+ *   - Return value: GBS_OK (0) or a negative status below.  A status other
+ *     than GBS_OK means nothing was launched, except GBS_ECUDA, which may
+ *     follow a failed launch.  gbs_last_error() gives a message for the
+ *     calling thread.
+ *   - The library does not check the values of row_ptr or col_idx on the
+ *     device unless asked (gbs_validate_csr, or a plan built with
+ *     GBS_PLAN_CHECK): malformed indices read out of bounds.
+ */
+#ifndef GBSPMV_H
+#define GBSPMV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define GBS_OK 0
+#define GBS_EINVAL (-1)       /* a size is negative, a required pointer is NULL, ld < k, ... */
+#define GBS_EALIGN (-2)       /* a pointer or leading dimension breaks a stated alignment rule */
+#define GBS_EDTYPE (-3)       /* unknown gbs_dtype */
+#define GBS_ECUDA (-4)        /* a CUDA runtime call or launch failed */
+#define GBS_EINDEX (-5)       /* CSR structure invalid (validation only) */
+#define GBS_ETIMEOUT (-6)     /* a bounded device-side wait gave up */
+#define GBS_ENOMEM (-7)       /* device or host allocation failed */
+#define GBS_EUNSUPPORTED (-8) /* valid request this build does not support */
+
+/* ------------------------------------------------------------------ types */
+typedef enum { GBS_F64 = 0, GBS_F32 = 1 } gbs_dtype;
+
+/* Kernel variants. */
+typedef enum {
+  GBS_VARIANT_AUTO = 0,   /* let the library choose from the row-length statistics */
+  GBS_VARIANT_ROWS = 1,   /* sub-warp per row: `lanes` lanes share one row */
+  GBS_VARIANT_MERGE = 2   /* merge-path: equal shares of (rows + nonzeros) per thread */
+} gbs_variant;
+
+/*
+ * Launch configuration of one product.  Zero fields mean "library default".
+ *   variant      gbs_variant.
+ *   lanes        ROWS: lanes per row, one of 1, 2, 4, 8, 16, 32.  For SpMV
+ *                the lanes split the row's nonzeros (then add their partial
+ *                sums); for SpMM (k > 1) they split the k columns.
+ *   threads      threads per CTA (multiple of 32, <= 1024).
+ *   tile_nnz     ROWS: nonzeros staged in shared memory per pass.
+ *   items        MERGE: merge-path items (rows + nonzeros) per thread.
+ */
+typedef struct {
+  int variant;
+  int lanes;
+  int threads;
+  int tile_nnz;
+  int items;
+} gbs_config;
+
+/* Row-length statistics computed on the device (gbs_csr_stats). */
+typedef struct {
+  int m, n, nnz;
+  int max_row;          /* longest row */
+  int empty_rows;       /* rows with no nonzero */
+  double mean_row;      /* nnz / m */
+  double cv_row;        /* coefficient of variation of row lengths */
+  long long rows_over_32, rows_over_256, rows_over_4096; /* counts of long rows */
+} gbs_stats;
+
+/* ------------------------------------------------------------- misc API */
+int gbs_version(void);                       /* 10000 * major + 100 * minor + patch */
+const char* gbs_status_string(int status);   /* static string */
+const char* gbs_last_error(void);            /* message of the last failure on this thread */
+
+/*
+ * Check a CSR structure on the device: row_ptr[0] == 0, row_ptr
+ * non-decreasing, row_ptr[m] == nnz, 0 <= col_idx[p] < n.  Synchronises
+ * `stream`.  Returns GBS_OK or GBS_EINDEX.
+ */
+int gbs_validate_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, void* stream);
+
+/*
+ * Row-length statistics of A (Sec. 4 Table "tab:matrices" lists the same
+ * quantities: rows, nonzeros, nnz/row, max nnz/row).  Synchronises `stream`;
+ * `out` is a host pointer.
+ */
+int gbs_csr_stats(int m, int n, int nnz, const int* row_ptr, gbs_stats* out, void* stream);
+
+/* The configuration the library would pick for these statistics and k (host only). */
+int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out);
+
+/*
+ * Diagnostic: FP64 fused-multiply-add throughput.  Launches `blocks` x
+ * `threads` threads that each run `iters` x 8 independent FMAs and write one
+ * double to out[blocks * threads] (device).  The caller times it: flops =
+ * 2 * 8 * iters * blocks * threads.  On GB300 the FP64 pipe is about 1/64
+ * of the FP32 rate, which makes it a second roof of FP64 SpMV beside HBM
+ * bandwidth (Sec. 4.1 notes that on the Xeon Phi the FP peak was not the
+ * bottleneck; here it can be).  The paper has no counterpart.
+ */
+int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream);
+
+/* ------------------------------------------------------------------ SpMV */
+/*
+ * y <- A x  (Sec. 3).  vals, x and y have type `dtype`; x has n entries and
+ * y has m entries.  The variant is chosen without looking at row_ptr
+ * (merge-path, which balances any row-length distribution); its scratch
+ * (one carry per CTA) comes from the stream-ordered allocator of the
+ * current device (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * m, n >= 0, nnz >= 0; nnz == 0 or m == 0 writes zeros / nothing.
+ */
+int spmv_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+             int dtype, const void* x, void* y, void* stream);
+
+/* As spmv_csr, with an explicit configuration (NULL = spmv_csr's choice). */
+int spmv_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+                 int dtype, const void* x, void* y, const gbs_config* cfg, void* stream);
+
+/* ------------------------------------------------------------------ SpMM */
+/*
+ * Y <- A X  (Sec. 5): X is n x k with leading dimension ldx >= k, Y is m x k
+ * with leading dimension ldy >= k, both row major, elements of `dtype`.
+ * k >= 1.  When X, Y and their leading dimensions are 16-byte aligned the
+ * gathers of X rows use 128-bit loads; otherwise narrower loads are used.
+ * Y is written with streaming (evict-first) stores.
+ */
+int spmm_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+             int dtype, int k, const void* X, int ldx, void* Y, int ldy, void* stream);
+
+int spmm_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+                 int dtype, int k, const void* X, int ldx, void* Y, int ldy, const gbs_config* cfg,
+                 void* stream);
+
+/* ------------------------------------------------------------------ plans */
+/*
+ * A plan fixes the structure (m, n, nnz, row_ptr, col_idx), the dtype and k,
+ * computes the row-length statistics, picks a configuration and owns any
+ * scratch it needs.  With GBS_PLAN_TUNE it times candidate configurations
+ * on the device (on scratch values it allocates itself) and keeps the
+ * fastest.  With GBS_PLAN_CHECK it validates the structure first.  The plan
+ * keeps row_ptr and col_idx as given: they must stay valid and unchanged
+ * while the plan is used.  gbs_plan_create synchronises `stream`.
+ * Executing a plan allocates nothing and can be captured in a CUDA graph.
+ */
+#define GBS_PLAN_TUNE 1
+#define GBS_PLAN_CHECK 2
+
+typedef struct gbs_plan gbs_plan;
+
+int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx,
+                    int dtype, int k, int flags, void* stream);
+int gbs_plan_destroy(gbs_plan* plan);
+int gbs_plan_get_config(const gbs_plan* plan, gbs_config* cfg);
+int gbs_plan_set_config(gbs_plan* plan, const gbs_config* cfg);
+int gbs_plan_get_stats(const gbs_plan* plan, gbs_stats* out);
+/* y <- A x (plan k must be 1) or Y <- A X (ldx, ldy >= plan k). */
+int spmv_csr_plan(const gbs_plan* plan, const void* vals, const void* x, void* y, void* stream);
+int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx, void* Y, int ldy,
+                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBSPMV_H */

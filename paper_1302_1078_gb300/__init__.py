@@ -1,0 +1,223 @@
+"""gbspmv: CSR SpMV / SpMM on GB300 (sm_103a) behind a C ABI.
+
+Thin Python binding over ``libgbspmv.so`` (see ``include/gbspmv.h``).  PyTorch
+supplies device memory and the current CUDA stream; every step of every
+product runs in the library's CUDA kernels.  The functions here only check
+and marshal arguments.  If the library cannot be loaded, every call raises:
+there is no CPU fallback.
+
+    y = spmv_csr(row_ptr, col_idx, vals, x)           # y <- A x      (paper Sec. 3)
+    Y = spmm_csr(row_ptr, col_idx, vals, X)           # Y <- A X, X row major n x k (Sec. 5)
+    plan = Plan(row_ptr, col_idx, n, dtype, k, tune=True); plan.spmv(vals, x, y)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _capi
+from ._capi import GbsError, gbs_config, gbs_stats  # noqa: F401
+
+__all__ = [
+    "spmv_csr", "spmm_csr", "Plan", "csr_stats", "validate_csr", "default_config", "GbsError", "lib",
+]
+
+
+def lib():
+    """The loaded C library (built on first use if needed)."""
+    return _capi.load()
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return _capi.GBS_F64
+    if t.dtype == torch.float32:
+        return _capi.GBS_F32
+    raise TypeError(f"values must be float64 or float32, got {t.dtype}")
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    return t.data_ptr() if t.numel() else 0
+
+
+def _stream(device: torch.device, stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream)
+
+
+def _need_cuda(*ts):
+    dev = None
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("gbspmv operates on CUDA tensors only")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError("all tensors must be on the same device")
+    return dev
+
+
+def _check_index(row_ptr: torch.Tensor, col_idx: torch.Tensor):
+    if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+        raise TypeError("row_ptr and col_idx must be int32")
+    if row_ptr.dim() != 1 or col_idx.dim() != 1 or not row_ptr.is_contiguous() or not col_idx.is_contiguous():
+        raise ValueError("row_ptr and col_idx must be contiguous 1-D tensors")
+
+
+def _config(cfg) -> gbs_config | None:
+    if cfg is None:
+        return None
+    if isinstance(cfg, gbs_config):
+        return cfg
+    c = gbs_config()
+    for k, v in dict(cfg).items():
+        setattr(c, k, int(v))
+    return c
+
+
+def spmv_csr(row_ptr, col_idx, vals, x, y=None, *, n: int | None = None, config=None, stream=None):
+    """y <- A x for the CSR matrix (row_ptr, col_idx, vals).  Returns y."""
+    _check_index(row_ptr, col_idx)
+    dev = _need_cuda(row_ptr, col_idx, vals, x, y)
+    dt = _dtype_code(vals)
+    if x.dtype != vals.dtype or x.dim() != 1 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous 1-D tensor of the values' dtype")
+    m = row_ptr.numel() - 1
+    n = x.numel() if n is None else n
+    if y is None:
+        y = torch.empty(m, dtype=vals.dtype, device=dev)
+    elif y.dtype != vals.dtype or y.numel() != m or not y.is_contiguous():
+        raise ValueError("y must be contiguous with m entries of the values' dtype")
+    L = lib()
+    c = _config(config)
+    s = _stream(dev, stream)
+    if c is None:
+        rc = L.spmv_csr(m, n, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), dt, _ptr(x), _ptr(y), s)
+    else:
+        rc = L.spmv_csr_cfg(m, n, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), dt, _ptr(x), _ptr(y),
+                            ctypes.byref(c), s)
+    _capi.check(rc, "spmv_csr")
+    return y
+
+
+def spmm_csr(row_ptr, col_idx, vals, X, Y=None, *, config=None, stream=None):
+    """Y <- A X with X an n x k row-major tensor (a row stride >= k is allowed).  Returns Y."""
+    _check_index(row_ptr, col_idx)
+    dev = _need_cuda(row_ptr, col_idx, vals, X, Y)
+    dt = _dtype_code(vals)
+    if X.dtype != vals.dtype or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be 2-D, row major, of the values' dtype")
+    m = row_ptr.numel() - 1
+    n, k = X.shape
+    if Y is None:
+        Y = torch.empty((m, k), dtype=vals.dtype, device=dev)
+    elif Y.dtype != vals.dtype or Y.dim() != 2 or Y.shape != (m, k) or Y.stride(1) != 1:
+        raise ValueError("Y must be m x k, row major, of the values' dtype")
+    L = lib()
+    c = _config(config)
+    s = _stream(dev, stream)
+    ldx, ldy = max(X.stride(0), k), max(Y.stride(0), k)
+    args = (m, n, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), dt, k, _ptr(X), ldx, _ptr(Y), ldy)
+    rc = L.spmm_csr(*args, s) if c is None else L.spmm_csr_cfg(*args, ctypes.byref(c), s)
+    _capi.check(rc, "spmm_csr")
+    return Y
+
+
+def csr_stats(row_ptr, n: int, nnz: int | None = None, stream=None) -> dict:
+    """Row-length statistics computed on the device."""
+    dev = _need_cuda(row_ptr)
+    m = row_ptr.numel() - 1
+    nnz = int(row_ptr[-1].item()) if nnz is None else nnz
+    st = gbs_stats()
+    _capi.check(lib().gbs_csr_stats(m, n, nnz, _ptr(row_ptr), ctypes.byref(st), _stream(dev, stream)), "gbs_csr_stats")
+    return st.as_dict()
+
+
+def validate_csr(row_ptr, col_idx, n: int, stream=None) -> None:
+    """Raise GbsError(GBS_EINDEX) if the CSR structure is malformed."""
+    dev = _need_cuda(row_ptr, col_idx)
+    m = row_ptr.numel() - 1
+    _capi.check(lib().gbs_validate_csr(m, n, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _stream(dev, stream)),
+                "gbs_validate_csr")
+
+
+def default_config(stats: dict, dtype: torch.dtype, k: int = 1) -> dict:
+    st = gbs_stats()
+    for key, v in stats.items():
+        setattr(st, key, v)
+    c = gbs_config()
+    dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
+    _capi.check(lib().gbs_default_config(ctypes.byref(st), dt, int(k), ctypes.byref(c)), "gbs_default_config")
+    return c.as_dict()
+
+
+class Plan:
+    """A fixed CSR structure with its chosen (optionally autotuned) configuration.
+
+    The plan keeps references to row_ptr and col_idx; executing it allocates nothing."""
+
+    def __init__(self, row_ptr, col_idx, n: int, dtype=torch.float64, k: int = 1, *, tune: bool = False,
+                 check: bool = False, config=None, stream=None):
+        _check_index(row_ptr, col_idx)
+        dev = _need_cuda(row_ptr, col_idx)
+        self.row_ptr, self.col_idx = row_ptr, col_idx
+        self.m, self.n, self.nnz, self.k = row_ptr.numel() - 1, int(n), col_idx.numel(), int(k)
+        self.dtype = dtype
+        self.device = dev
+        self._h = ctypes.c_void_p()
+        flags = (_capi.PLAN_TUNE if tune else 0) | (_capi.PLAN_CHECK if check else 0)
+        dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
+        _capi.check(lib().gbs_plan_create(ctypes.byref(self._h), self.m, self.n, self.nnz, _ptr(row_ptr),
+                                          _ptr(col_idx), dt, self.k, flags, _stream(dev, stream)), "gbs_plan_create")
+        if config is not None:
+            self.set_config(config)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().gbs_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def config(self) -> dict:
+        c = gbs_config()
+        _capi.check(lib().gbs_plan_get_config(self._h, ctypes.byref(c)), "gbs_plan_get_config")
+        return c.as_dict()
+
+    def set_config(self, cfg) -> None:
+        _capi.check(lib().gbs_plan_set_config(self._h, ctypes.byref(_config(cfg))), "gbs_plan_set_config")
+
+    @property
+    def stats(self) -> dict:
+        st = gbs_stats()
+        _capi.check(lib().gbs_plan_get_stats(self._h, ctypes.byref(st)), "gbs_plan_get_stats")
+        return st.as_dict()
+
+    def spmv(self, vals, x, y=None, stream=None):
+        _need_cuda(vals, x, y)
+        if y is None:
+            y = torch.empty(self.m, dtype=self.dtype, device=self.device)
+        if vals.dtype != self.dtype or x.dtype != self.dtype or y.dtype != self.dtype:
+            raise TypeError("dtype differs from the plan's")
+        _capi.check(lib().spmv_csr_plan(self._h, _ptr(vals), _ptr(x), _ptr(y), _stream(self.device, stream)),
+                    "spmv_csr_plan")
+        return y
+
+    def spmm(self, vals, X, Y=None, stream=None):
+        _need_cuda(vals, X, Y)
+        if X.dim() != 2 or X.shape[1] != self.k or X.stride(1) != 1:
+            raise ValueError("X must be n x k row major")
+        if Y is None:
+            Y = torch.empty((self.m, self.k), dtype=self.dtype, device=self.device)
+        _capi.check(lib().spmm_csr_plan(self._h, _ptr(vals), _ptr(X), max(X.stride(0), self.k), _ptr(Y),
+                                        max(Y.stride(0), self.k), _stream(self.device, stream)), "spmm_csr_plan")
+        return Y

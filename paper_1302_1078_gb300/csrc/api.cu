@@ -1,0 +1,712 @@
+// C-ABI entry points of gbspmv (declared in include/gbspmv.h): argument
+// checks, configuration choice, plans, the autotuner, CSR statistics and
+// validation.  Every product runs in the kernels of rows_kernel.cuh and
+// merge_kernel.cuh; nothing here computes on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbspmv.h"
+#include "launch.h"
+#include "merge_kernel.cuh"
+#include "rows_kernel.cuh"
+
+using namespace gbs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return GBS_ECUDA;
+}
+
+bool valid_dtype(int d) { return d == GBS_F64 || d == GBS_F32; }
+size_t dsize(int d) { return d == GBS_F64 ? 8 : 4; }
+int vec_of(int d) { return d == GBS_F64 ? 2 : 4; }
+bool pow2_lanes(int l) { return l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32; }
+int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int check_csr(int m, int n, int nnz, const int* rp, const int* ci, const void* vals) {
+  if (m < 0 || n < 0 || nnz < 0) return fail(GBS_EINVAL, "negative size");
+  if (m > 0 && rp == nullptr) return fail(GBS_EINVAL, "row_ptr is NULL");
+  if (nnz > 0 && (ci == nullptr || vals == nullptr)) return fail(GBS_EINVAL, "col_idx or vals is NULL");
+  if ((long long)m + nnz > 0x7fffffffLL) return fail(GBS_EUNSUPPORTED, "m + nnz must be below 2^31");
+  return GBS_OK;
+}
+
+bool checked_mode() {
+  const char* e = std::getenv("GBSPMV_CHECKED");
+  return e && e[0] && e[0] != '0';
+}
+
+// Columns handled by one launch: 32 lanes x VEC (128-bit) or 32 lanes x 1.
+int panel_cols(int dtype, bool vec16) { return 32 * (vec16 ? vec_of(dtype) : 1); }
+
+// Lanes that cover kp columns.
+int col_lanes(int kp, int dtype, bool vec16) {
+  int v = vec16 ? vec_of(dtype) : 1;
+  return std::min(32, pow2ceil((kp + v - 1) / v));
+}
+
+bool dense_vec16(int dtype, int k, const void* X, long long ldx, const void* Y, long long ldy) {
+  if (k <= 1) return false;
+  const size_t es = dsize(dtype);
+  return aligned16(X) && aligned16(Y) && ((ldx * (long long)es) % 16 == 0) && ((ldy * (long long)es) % 16 == 0);
+}
+
+int default_items(int g, int threads) { return std::max(4, (2048 * g) / threads); }
+
+gbs_config normalize(const gbs_config& c, int dtype) {
+  gbs_config r = c;
+  if (r.threads <= 0) r.threads = 256;
+  if (r.variant == GBS_VARIANT_ROWS) {
+    if (r.lanes <= 0) r.lanes = 1;
+    if (r.tile_nnz <= 0) r.tile_nnz = dtype == GBS_F64 ? 2048 : 3072;
+  }
+  return r;
+}
+
+// Merge geometry of one call: lanes per merge thread (columns), items per merge thread, CTAs.
+struct MergeGeom {
+  int g, items, ctas, kp_max;
+};
+
+int check_cfg(const gbs_config& c) {
+  if (c.variant != GBS_VARIANT_ROWS && c.variant != GBS_VARIANT_MERGE)
+    return fail(GBS_EINVAL, "variant must be ROWS or MERGE after resolution");
+  if (c.threads % 32 != 0 || c.threads < 32 || c.threads > 1024) return fail(GBS_EINVAL, "threads must be 32..1024, multiple of 32");
+  if (c.variant == GBS_VARIANT_MERGE && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
+  if (c.lanes != 0 && !pow2_lanes(c.lanes)) return fail(GBS_EINVAL, "lanes must be 1, 2, 4, 8, 16 or 32");
+  if (c.variant == GBS_VARIANT_ROWS && (c.tile_nnz < 32 || c.tile_nnz > (1 << 16)))
+    return fail(GBS_EINVAL, "tile_nnz must be in [32, 65536]");
+  if (c.variant == GBS_VARIANT_MERGE && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
+  return GBS_OK;
+}
+
+// ---------------------------------------------------------------- execution
+
+struct MergeBuffers {
+  MergeScratch s{};
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+size_t merge_scratch_bytes(int ctas, int kp, int dtype) {
+  size_t a = ((size_t)(ctas + 1) * sizeof(int2) + 255) & ~(size_t)255;
+  size_t b = ((size_t)ctas * sizeof(int) + 255) & ~(size_t)255;
+  size_t c = (size_t)ctas * std::max(kp, 1) * dsize(dtype);
+  return a + b + c;
+}
+
+void merge_carve(MergeBuffers& mb, int ctas, int kp, int dtype) {
+  char* p = static_cast<char*>(mb.base);
+  mb.s.ctas = ctas;
+  mb.s.coords = reinterpret_cast<int2*>(p);
+  p += ((size_t)(ctas + 1) * sizeof(int2) + 255) & ~(size_t)255;
+  mb.s.carry_row = reinterpret_cast<int*>(p);
+  p += ((size_t)ctas * sizeof(int) + 255) & ~(size_t)255;
+  mb.s.carry_val = p;
+  (void)kp;
+  (void)dtype;
+}
+
+int merge_ctas(int m, int nnz, int threads, int g, int items) {
+  long long ipc = (long long)(threads / g) * items;
+  long long total = (long long)m + nnz;
+  return (int)std::max<long long>(1, (total + ipc - 1) / ipc);
+}
+
+MergeGeom merge_geom(const gbs_config& cfg, int m, int nnz, int dtype, int k, bool vec16) {
+  MergeGeom g{};
+  g.kp_max = std::min(panel_cols(dtype, vec16), k);
+  g.g = k == 1 ? 1 : std::max(cfg.lanes > 0 ? cfg.lanes : 1, col_lanes(g.kp_max, dtype, vec16));
+  g.g = std::min(g.g, cfg.threads);
+  g.items = cfg.items > 0 ? cfg.items : default_items(g.g, cfg.threads);
+  g.ctas = merge_ctas(m, nnz, cfg.threads, g.g, g.items);
+  return g;
+}
+
+// Run one product Y = A X (k >= 1; k == 1 with ldx = ldy = 1 is SpMV) with a resolved
+// configuration.  Merge scratch comes from `mb` if given (plan), else from the stream-ordered
+// allocator.  `coords_ready`: the partition in mb is valid for this configuration.
+int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx, void* Y, long long ldy,
+                const gbs_config& cfg, MergeBuffers* mb, bool coords_ready, cudaStream_t s) {
+  if (A.m == 0 || k == 0) return GBS_OK;
+  const bool vec16 = dense_vec16(dtype, k, X, ldx, Y, ldy);
+  const int P = panel_cols(dtype, vec16);
+  const size_t es = dsize(dtype);
+  cudaError_t e = cudaSuccess;
+  if (cfg.variant == GBS_VARIANT_ROWS) {
+    for (int c0 = 0; c0 < k; c0 += P) {
+      const int kp = std::min(P, k - c0);
+      int lanes = cfg.lanes;
+      if (k > 1) lanes = std::max(lanes, col_lanes(kp, dtype, vec16));
+      DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
+      e = dtype == GBS_F64 ? launch_rows_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, A.m, s)
+                           : launch_rows_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, A.m, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ROWS launch");
+    }
+    return GBS_OK;
+  }
+  // MERGE
+  const MergeGeom G = merge_geom(cfg, A.m, A.nnz, dtype, k, vec16);
+  const int kp_max = G.kp_max, g = G.g, ctas = G.ctas;
+  MergeBuffers local;
+  MergeBuffers* use = mb;
+  if (use == nullptr) {
+    local.bytes = merge_scratch_bytes(ctas, kp_max, dtype);
+    e = cudaMallocAsync(&local.base, local.bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (merge scratch)");
+    merge_carve(local, ctas, kp_max, dtype);
+    use = &local;
+    coords_ready = false;
+  } else if (use->s.ctas != ctas) {
+    return fail(GBS_EINVAL, "plan scratch does not match the configuration");
+  }
+  int rc = GBS_OK;
+  if (!coords_ready) {
+    e = launch_merge_partition(A, (long long)(cfg.threads / g) * G.items, use->s, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "merge partition");
+  }
+  for (int c0 = 0; rc == GBS_OK && c0 < k; c0 += P) {
+    const int kp = std::min(P, k - c0);
+    DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
+    e = dtype == GBS_F64 ? launch_merge_f64(A, D, g, vec16, cfg.threads, G.items, use->s, s)
+                         : launch_merge_f32(A, D, g, vec16, cfg.threads, G.items, use->s, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "MERGE launch");
+  }
+  if (use == &local) {
+    e = cudaFreeAsync(local.base, s);
+    if (e != cudaSuccess && rc == GBS_OK) rc = cuda_fail(e, "cudaFreeAsync");
+  }
+  return rc;
+}
+
+// --------------------------------------------------------------- statistics
+
+__global__ void stats_kernel(const int* __restrict__ rp, int m, unsigned long long* __restrict__ acc, int* __restrict__ maxrow) {
+  unsigned long long sq = 0, empty = 0, o32 = 0, o256 = 0, o4k = 0;
+  int mx = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int len = rp[i + 1] - rp[i];
+    sq += (unsigned long long)len * (unsigned long long)len;
+    empty += len == 0;
+    o32 += len > 32;
+    o256 += len > 256;
+    o4k += len > 4096;
+    mx = max(mx, len);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    empty += __shfl_xor_sync(0xffffffffu, empty, o);
+    o32 += __shfl_xor_sync(0xffffffffu, o32, o);
+    o256 += __shfl_xor_sync(0xffffffffu, o256, o);
+    o4k += __shfl_xor_sync(0xffffffffu, o4k, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc + 0, sq);
+    atomicAdd(acc + 1, empty);
+    atomicAdd(acc + 2, o32);
+    atomicAdd(acc + 3, o256);
+    atomicAdd(acc + 4, o4k);
+    atomicMax(maxrow, mx);
+  }
+}
+
+__global__ void validate_kernel(const int* __restrict__ rp, const int* __restrict__ ci, int m, int n, int nnz,
+                                int* __restrict__ flags) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  int f = 0;
+  if (tid == 0) {
+    if (rp[0] != 0) f |= 1;
+    if (rp[m] != nnz) f |= 2;
+  }
+  for (int i = tid; i < m; i += nt)
+    if (rp[i + 1] < rp[i]) f |= 4;
+  for (int p = tid; p < nnz; p += nt) {
+    const int c = ci[p];
+    if (c < 0 || c >= n) f |= 8;
+  }
+  if (f) atomicOr(flags, f);
+}
+
+int compute_stats(int m, int n, int nnz, const int* rp, gbs_stats* out, cudaStream_t s) {
+  std::memset(out, 0, sizeof(*out));
+  out->m = m;
+  out->n = n;
+  out->nnz = nnz;
+  if (m == 0) return GBS_OK;
+  void* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, 64, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (stats)");
+  unsigned long long* acc = static_cast<unsigned long long*>(buf);
+  int* mx = reinterpret_cast<int*>(acc + 5);
+  unsigned long long h[5];
+  int hm = 0;
+  e = cudaMemsetAsync(buf, 0, 64, s);
+  if (e == cudaSuccess) {
+    int blocks = std::min(1024, (m + 255) / 256);
+    stats_kernel<<<blocks, 256, 0, s>>>(rp, m, acc, mx);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, mx, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "CSR statistics");
+  out->max_row = hm;
+  out->empty_rows = (int)h[1];
+  out->mean_row = (double)nnz / m;
+  double var = (double)h[0] / m - out->mean_row * out->mean_row;
+  out->cv_row = out->mean_row > 0 ? std::sqrt(std::max(0.0, var)) / out->mean_row : 0.0;
+  out->rows_over_32 = (long long)h[2];
+  out->rows_over_256 = (long long)h[3];
+  out->rows_over_4096 = (long long)h[4];
+  return GBS_OK;
+}
+
+gbs_config heuristic_config(const gbs_stats& st, int dtype, int k) {
+  gbs_config c{};
+  c.threads = 256;
+  const double mean = st.mean_row;
+  const bool skewed = st.max_row > 16.0 * mean + 256.0 || st.cv_row > 2.0;
+  if (skewed) {
+    c.variant = GBS_VARIANT_MERGE;
+    c.lanes = 0;
+    c.items = 0;
+  } else {
+    c.variant = GBS_VARIANT_ROWS;
+    if (k == 1) {
+      // FP64: one lane per row keeps every FMA lane busy and needs no reduction;
+      // long rows get more lanes so that a warp's rows finish together.
+      const double per = dtype == GBS_F64 ? 64.0 : 16.0;
+      int l = 1;
+      while (l < 32 && mean > per * l) l <<= 1;
+      c.lanes = l;
+    } else {
+      c.lanes = 0;  // column lanes follow k
+    }
+    c.tile_nnz = dtype == GBS_F64 ? 2048 : 3072;
+  }
+  return normalize(c, dtype);
+}
+
+// Eight independent FMA chains per thread: the FP64 pipe's throughput, not its latency.
+__global__ void fp64_probe_kernel(double* __restrict__ out, int iters) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+  const double b = 0.999999, c = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c);
+    a1 = fma(a1, b, c);
+    a2 = fma(a2, b, c);
+    a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c);
+    a5 = fma(a5, b, c);
+    a6 = fma(a6, b, c);
+    a7 = fma(a7, b, c);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace
+
+namespace gbs {
+// Start coordinates of every merge-path tile: one thread per tile boundary.
+__global__ void merge_partition_kernel(const int* __restrict__ row_ptr, int m, int nnz, int ctas,
+                                       long long items_per_cta, int2* __restrict__ coords) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > ctas) return;
+  long long total = (long long)m + nnz;
+  long long d = (long long)b * items_per_cta;
+  if (d > total) d = total;
+  coords[b] = merge_search_global(row_ptr, m, nnz, d);
+}
+
+cudaError_t launch_merge_partition(const CsrView& A, long long items_per_cta, const MergeScratch& S, cudaStream_t s) {
+  const int n = S.ctas + 1;
+  merge_partition_kernel<<<(n + 255) / 256, 256, 0, s>>>(A.row_ptr, A.m, A.nnz, S.ctas, items_per_cta, S.coords);
+  return cudaGetLastError();
+}
+}  // namespace gbs
+
+// ====================================================================== ABI
+
+extern "C" {
+
+int gbs_version(void) { return 100; }
+
+int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream) {
+  if (!out || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || iters < 1)
+    return fail(GBS_EINVAL, "fp64 probe arguments");
+  fp64_probe_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(out, iters);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "fp64 probe");
+}
+
+const char* gbs_status_string(int status) {
+  switch (status) {
+    case GBS_OK: return "ok";
+    case GBS_EINVAL: return "invalid argument";
+    case GBS_EALIGN: return "misaligned pointer or leading dimension";
+    case GBS_EDTYPE: return "unknown dtype";
+    case GBS_ECUDA: return "CUDA error";
+    case GBS_EINDEX: return "invalid CSR structure";
+    case GBS_ETIMEOUT: return "device wait timed out";
+    case GBS_ENOMEM: return "out of memory";
+    case GBS_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* gbs_last_error(void) { return g_err.c_str(); }
+
+int gbs_validate_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, void* stream) {
+  if (m < 0 || n < 0 || nnz < 0) return fail(GBS_EINVAL, "negative size");
+  if (row_ptr == nullptr || (nnz > 0 && col_idx == nullptr)) return fail(GBS_EINVAL, "NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* flags = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&flags), sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (validate)");
+  int h = 0;
+  e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    long long work = std::max<long long>(m, nnz);
+    int blocks = (int)std::min<long long>(2048, std::max<long long>(1, (work + 255) / 256));
+    validate_kernel<<<blocks, 256, 0, s>>>(row_ptr, col_idx, m, n, nnz, flags);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(flags, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "validate");
+  if (h) {
+    std::string msg = "invalid CSR:";
+    if (h & 1) msg += " row_ptr[0] != 0;";
+    if (h & 2) msg += " row_ptr[m] != nnz;";
+    if (h & 4) msg += " row_ptr decreases;";
+    if (h & 8) msg += " col_idx outside [0, n);";
+    return fail(GBS_EINDEX, msg);
+  }
+  return GBS_OK;
+}
+
+int gbs_csr_stats(int m, int n, int nnz, const int* row_ptr, gbs_stats* out, void* stream) {
+  if (out == nullptr) return fail(GBS_EINVAL, "out is NULL");
+  int rc = check_csr(m, n, nnz, row_ptr, reinterpret_cast<const int*>(1), reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  return compute_stats(m, n, nnz, row_ptr, out, static_cast<cudaStream_t>(stream));
+}
+
+int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out) {
+  if (stats == nullptr || out == nullptr) return fail(GBS_EINVAL, "NULL pointer");
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  *out = heuristic_config(*stats, dtype, k);
+  return GBS_OK;
+}
+
+static int product_entry(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                         int k, const void* X, long long ldx, void* Y, long long ldy, const gbs_config* cfg,
+                         void* stream) {
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype must be GBS_F64 or GBS_F32");
+  int rc = check_csr(m, n, nnz, row_ptr, col_idx, vals);
+  if (rc) return rc;
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  if (ldx < k || ldy < k) return fail(GBS_EINVAL, "leading dimension smaller than k");
+  if (m > 0 && Y == nullptr) return fail(GBS_EINVAL, "y/Y is NULL");
+  if (nnz > 0 && X == nullptr) return fail(GBS_EINVAL, "x/X is NULL");
+  const size_t es = dsize(dtype);
+  if ((reinterpret_cast<uintptr_t>(vals) % es) || (reinterpret_cast<uintptr_t>(X) % es) ||
+      (reinterpret_cast<uintptr_t>(Y) % es) || (reinterpret_cast<uintptr_t>(col_idx) % 4) ||
+      (reinterpret_cast<uintptr_t>(row_ptr) % 4))
+    return fail(GBS_EALIGN, "arrays must be aligned to their element size");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (checked_mode()) {
+    rc = gbs_validate_csr(m, n, nnz, row_ptr, col_idx, stream);
+    if (rc) return rc;
+  }
+  gbs_config c{};
+  if (cfg == nullptr || cfg->variant == GBS_VARIANT_AUTO) {
+    c.variant = GBS_VARIANT_MERGE;
+    c.threads = cfg && cfg->threads ? cfg->threads : 256;
+    c.items = cfg ? cfg->items : 0;
+    c.lanes = cfg ? cfg->lanes : 0;
+    c.tile_nnz = 0;
+  } else {
+    c = *cfg;
+  }
+  c = normalize(c, dtype);
+  rc = check_cfg(c);
+  if (rc) return rc;
+  CsrView A{m, n, nnz, row_ptr, col_idx, vals};
+  return run_product(A, dtype, k, X, ldx, Y, ldy, c, nullptr, false, s);
+}
+
+int spmv_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+             const void* x, void* y, void* stream) {
+  return product_entry(m, n, nnz, row_ptr, col_idx, vals, dtype, 1, x, 1, y, 1, nullptr, stream);
+}
+
+int spmv_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                 const void* x, void* y, const gbs_config* cfg, void* stream) {
+  return product_entry(m, n, nnz, row_ptr, col_idx, vals, dtype, 1, x, 1, y, 1, cfg, stream);
+}
+
+int spmm_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype, int k,
+             const void* X, int ldx, void* Y, int ldy, void* stream) {
+  return product_entry(m, n, nnz, row_ptr, col_idx, vals, dtype, k, X, ldx, Y, ldy, nullptr, stream);
+}
+
+int spmm_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype, int k,
+                 const void* X, int ldx, void* Y, int ldy, const gbs_config* cfg, void* stream) {
+  return product_entry(m, n, nnz, row_ptr, col_idx, vals, dtype, k, X, ldx, Y, ldy, cfg, stream);
+}
+
+}  // extern "C"
+
+// ==================================================================== plans
+
+struct gbs_plan {
+  int m = 0, n = 0, nnz = 0, k = 1, dtype = GBS_F64, device = 0;
+  const int* row_ptr = nullptr;
+  const int* col_idx = nullptr;
+  gbs_stats stats{};
+  gbs_config cfg{};
+  MergeBuffers mb{};
+  bool coords_ready = false;
+};
+
+namespace {
+
+// Allocate (or free) the plan's merge scratch for its configuration and compute the
+// partition.  Scratch is sized for 128-bit column panels, the widest case.
+int plan_prepare(gbs_plan* p, cudaStream_t s) {
+  if (p->mb.base) {
+    cudaFree(p->mb.base);
+    p->mb = MergeBuffers{};
+  }
+  p->coords_ready = false;
+  if (p->cfg.variant != GBS_VARIANT_MERGE || p->m == 0) return GBS_OK;
+  // the partition depends on the lanes per merge thread, which depend on whether a call
+  // can use 128-bit column access; the plan is made for that case (k > 1) and calls that
+  // cannot use it take the stream-ordered path
+  const MergeGeom G = merge_geom(p->cfg, p->m, p->nnz, p->dtype, p->k, p->k > 1);
+  p->mb.bytes = merge_scratch_bytes(G.ctas, G.kp_max, p->dtype);
+  cudaError_t e = cudaMalloc(&p->mb.base, p->mb.bytes);
+  if (e != cudaSuccess) {
+    p->mb = MergeBuffers{};
+    return cuda_fail(e, "cudaMalloc (plan scratch)");
+  }
+  merge_carve(p->mb, G.ctas, G.kp_max, p->dtype);
+  CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, nullptr};
+  e = launch_merge_partition(A, (long long)(p->cfg.threads / G.g) * G.items, p->mb.s, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "merge partition");
+  p->coords_ready = true;
+  return GBS_OK;
+}
+
+int plan_run(const gbs_plan* p, const void* vals, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t s) {
+  CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, vals};
+  if (p->cfg.variant == GBS_VARIANT_MERGE) {
+    // the partition was made for 128-bit column access; if this call cannot use it the
+    // lane count differs and the stream-ordered path is used instead
+    const bool vec16 = dense_vec16(p->dtype, p->k, X, ldx, Y, ldy);
+    if (p->k > 1 && !vec16) return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s);
+    MergeBuffers mb = p->mb;
+    return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, &mb, p->coords_ready, s);
+  }
+  return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s);
+}
+
+// Candidate configurations for the tuner.
+std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
+  std::vector<gbs_config> c;
+  auto add = [&](int variant, int lanes, int threads, int tile, int items) {
+    gbs_config g{};
+    g.variant = variant;
+    g.lanes = lanes;
+    g.threads = threads;
+    g.tile_nnz = tile;
+    g.items = items;
+    c.push_back(normalize(g, p->dtype));
+  };
+  const int base_tile = p->dtype == GBS_F64 ? 2048 : 3072;
+  if (p->k == 1) {
+    for (int l : {1, 2, 4, 8, 16, 32}) {
+      if (l > 1 && p->stats.mean_row < 0.5 * l) continue;
+      add(GBS_VARIANT_ROWS, l, 256, base_tile, 0);
+    }
+    add(GBS_VARIANT_ROWS, 1, 128, base_tile, 0);
+    add(GBS_VARIANT_ROWS, 1, 256, base_tile * 2, 0);
+    for (int it : {4, 8, 16}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
+  } else {
+    add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
+    add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
+    add(GBS_VARIANT_ROWS, 0, 256, base_tile / 2, 0);
+    add(GBS_VARIANT_MERGE, 0, 256, 0, 0);
+    add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
+  }
+  return c;
+}
+
+int plan_tune(gbs_plan* p, cudaStream_t s) {
+  const size_t es = dsize(p->dtype);
+  const long long ld = p->k == 1 ? 1 : ((p->k + 1) / 2 * 2);  // even leading dimension keeps 16-byte rows for f64
+  const long long ldp = p->dtype == GBS_F64 ? ld : ((p->k + 3) / 4 * 4);
+  void *vals = nullptr, *X = nullptr, *Y = nullptr;
+  size_t bv = std::max<size_t>(16, (size_t)p->nnz * es);
+  size_t bx = std::max<size_t>(16, (size_t)p->n * (p->k == 1 ? 1 : ldp) * es);
+  size_t by = std::max<size_t>(16, (size_t)p->m * (p->k == 1 ? 1 : ldp) * es);
+  cudaError_t e = cudaMalloc(&vals, bv);
+  if (e == cudaSuccess) e = cudaMalloc(&X, bx);
+  if (e == cudaSuccess) e = cudaMalloc(&Y, by);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vals, 0, bv, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, bx, s);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  int rc = e == cudaSuccess ? GBS_OK : cuda_fail(e, "tuner allocation");
+  const long long ldx = p->k == 1 ? 1 : ldp;
+  float best = 1e30f;
+  gbs_config best_cfg = p->cfg;
+  if (rc == GBS_OK) {
+    for (const gbs_config& c : tune_candidates(p)) {
+      if (check_cfg(c) != GBS_OK) continue;
+      p->cfg = c;
+      if (plan_prepare(p, s) != GBS_OK) continue;
+      float times[3];
+      bool ok = true;
+      for (int r = 0; r < 4 && ok; ++r) {
+        if (cudaEventRecord(ev0, s) != cudaSuccess) ok = false;
+        if (ok && plan_run(p, vals, X, ldx, Y, ldx, s) != GBS_OK) ok = false;
+        if (ok && cudaEventRecord(ev1, s) != cudaSuccess) ok = false;
+        if (ok && cudaEventSynchronize(ev1) != cudaSuccess) ok = false;
+        float ms = 0;
+        if (ok) cudaEventElapsedTime(&ms, ev0, ev1);
+        if (r > 0) times[r - 1] = ms;
+      }
+      if (!ok) continue;
+      std::sort(times, times + 3);
+      if (times[1] < best) {
+        best = times[1];
+        best_cfg = c;
+      }
+    }
+    p->cfg = best_cfg;
+    rc = plan_prepare(p, s);
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  cudaFree(vals);
+  cudaFree(X);
+  cudaFree(Y);
+  g_err.clear();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx, int dtype, int k,
+                    int flags, void* stream) {
+  if (plan == nullptr) return fail(GBS_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  int rc = check_csr(m, n, nnz, row_ptr, col_idx, reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((flags & GBS_PLAN_CHECK) || checked_mode()) {
+    rc = gbs_validate_csr(m, n, nnz, row_ptr, col_idx, stream);
+    if (rc) return rc;
+  }
+  gbs_plan* p = new (std::nothrow) gbs_plan();
+  if (!p) return fail(GBS_ENOMEM, "host allocation");
+  p->m = m;
+  p->n = n;
+  p->nnz = nnz;
+  p->k = k;
+  p->dtype = dtype;
+  p->row_ptr = row_ptr;
+  p->col_idx = col_idx;
+  cudaGetDevice(&p->device);
+  rc = compute_stats(m, n, nnz, row_ptr, &p->stats, s);
+  if (rc == GBS_OK) {
+    p->cfg = heuristic_config(p->stats, dtype, k);
+    rc = (flags & GBS_PLAN_TUNE) && m > 0 ? plan_tune(p, s) : plan_prepare(p, s);
+  }
+  if (rc != GBS_OK) {
+    if (p->mb.base) cudaFree(p->mb.base);
+    delete p;
+    return rc;
+  }
+  *plan = p;
+  return GBS_OK;
+}
+
+int gbs_plan_destroy(gbs_plan* plan) {
+  if (!plan) return GBS_OK;
+  if (plan->mb.base) cudaFree(plan->mb.base);
+  delete plan;
+  return GBS_OK;
+}
+
+int gbs_plan_get_config(const gbs_plan* plan, gbs_config* cfg) {
+  if (!plan || !cfg) return fail(GBS_EINVAL, "NULL pointer");
+  *cfg = plan->cfg;
+  return GBS_OK;
+}
+
+int gbs_plan_get_stats(const gbs_plan* plan, gbs_stats* out) {
+  if (!plan || !out) return fail(GBS_EINVAL, "NULL pointer");
+  *out = plan->stats;
+  return GBS_OK;
+}
+
+int gbs_plan_set_config(gbs_plan* plan, const gbs_config* cfg) {
+  if (!plan || !cfg) return fail(GBS_EINVAL, "NULL pointer");
+  gbs_config c = cfg->variant == GBS_VARIANT_AUTO ? heuristic_config(plan->stats, plan->dtype, plan->k)
+                                                  : normalize(*cfg, plan->dtype);
+  int rc = check_cfg(c);
+  if (rc) return rc;
+  plan->cfg = c;
+  return plan_prepare(plan, nullptr);
+}
+
+int spmv_csr_plan(const gbs_plan* plan, const void* vals, const void* x, void* y, void* stream) {
+  if (!plan) return fail(GBS_EINVAL, "plan is NULL");
+  if (plan->k != 1) return fail(GBS_EINVAL, "plan was made for k > 1: use spmm_csr_plan");
+  if ((plan->nnz > 0 && (!vals || !x)) || (plan->m > 0 && !y)) return fail(GBS_EINVAL, "NULL pointer");
+  return plan_run(plan, vals, x, 1, y, 1, static_cast<cudaStream_t>(stream));
+}
+
+int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx, void* Y, int ldy, void* stream) {
+  if (!plan) return fail(GBS_EINVAL, "plan is NULL");
+  if (ldx < plan->k || ldy < plan->k) return fail(GBS_EINVAL, "leading dimension smaller than k");
+  if ((plan->nnz > 0 && (!vals || !X)) || (plan->m > 0 && !Y)) return fail(GBS_EINVAL, "NULL pointer");
+  return plan_run(plan, vals, X, ldx, Y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

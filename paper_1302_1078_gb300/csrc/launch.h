@@ -1,0 +1,51 @@
+// Internal launcher interface between the C-ABI layer (api.cu) and the
+// per-dtype kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace gbs {
+
+struct CsrView {
+  int m, n, nnz;
+  const int* row_ptr;
+  const int* col_idx;
+  const void* vals;
+};
+
+struct DenseView {
+  int k;
+  const void* X;
+  long long ldx;
+  void* Y;
+  long long ldy;
+};
+
+struct MergeScratch {
+  int ctas;
+  int2* coords;     // [ctas + 1]
+  int* carry_row;   // [ctas]
+  void* carry_val;  // [ctas * k] elements of the dtype
+};
+
+// ROWS variant.  lanes: 1..32 (power of two); k == 1 -> lanes split nonzeros,
+// k > 1 -> lanes split columns (k <= lanes * VEC is required per launch;
+// wider k is done in column panels by the caller).  vec16: use 128-bit
+// gathers/stores of X/Y (caller checked the alignment).
+cudaError_t launch_rows_f64(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                            int row_base, int rows, cudaStream_t s);
+cudaError_t launch_rows_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                            int row_base, int rows, cudaStream_t s);
+
+// MERGE variant: partition (coords) must have been computed for (threads / g) * items
+// items per CTA.  g lanes per merge thread (columns), g * VEC >= k.
+cudaError_t launch_merge_f64(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
+                             const MergeScratch& S, cudaStream_t s);
+cudaError_t launch_merge_f32(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
+                             const MergeScratch& S, cudaStream_t s);
+cudaError_t launch_merge_partition(const CsrView& A, long long items_per_cta, const MergeScratch& S, cudaStream_t s);
+
+// Shared-memory bytes of one CTA (host helpers).
+size_t rows_smem(int dtype, int rows_per_cta, int tile);
+size_t merge_smem(int dtype, int g, bool vec16, int threads, int items);
+
+}  // namespace gbs

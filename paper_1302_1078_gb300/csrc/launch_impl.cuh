@@ -1,0 +1,135 @@
+// Template launchers behind launch.h, instantiated once per dtype in
+// kernels_f64.cu / kernels_f32.cu so that the two compile in parallel.
+#pragma once
+#include "launch.h"
+#include "merge_kernel.cuh"
+#include "rows_kernel.cuh"
+
+namespace gbs {
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int VEC, int LANES, bool SPLIT>
+static cudaError_t rows_go(const RowsArgs<T>& a, int grid, int threads, size_t smem, cudaStream_t s) {
+  auto kern = rows_kernel<T, VEC, LANES, SPLIT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int LANES>
+static cudaError_t rows_lanes(const RowsArgs<T>& a, bool split, bool vec16, int grid, int threads, size_t smem,
+                              cudaStream_t s) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if (split) return rows_go<T, 1, LANES, true>(a, grid, threads, smem, s);
+  if (vec16) return rows_go<T, V, LANES, false>(a, grid, threads, smem, s);
+  return rows_go<T, 1, LANES, false>(a, grid, threads, smem, s);
+}
+
+template <typename T>
+cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                          int row_base, int rows, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  RowsArgs<T> a;
+  a.m = row_base + rows;
+  a.k = D.k;
+  a.row_ptr = A.row_ptr;
+  a.col_idx = A.col_idx;
+  a.vals = static_cast<const T*>(A.vals);
+  a.X = static_cast<const T*>(D.X);
+  a.Y = static_cast<T*>(D.Y);
+  a.ldx = D.ldx;
+  a.ldy = D.ldy;
+  a.tile = tile;
+  a.row_base = row_base;
+  a.aligned_vals = (reinterpret_cast<uintptr_t>(A.vals) & 15) == 0;
+  a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
+  const int rpc = threads / lanes;
+  const int grid = (rows + rpc - 1) / rpc;
+  const size_t smem = rows_smem_bytes<T>(rpc, tile);
+  const bool split = D.k == 1;
+  switch (lanes) {
+    case 1: return rows_lanes<T, 1>(a, split, vec16, grid, threads, smem, s);
+    case 2: return rows_lanes<T, 2>(a, split, vec16, grid, threads, smem, s);
+    case 4: return rows_lanes<T, 4>(a, split, vec16, grid, threads, smem, s);
+    case 8: return rows_lanes<T, 8>(a, split, vec16, grid, threads, smem, s);
+    case 16: return rows_lanes<T, 16>(a, split, vec16, grid, threads, smem, s);
+    case 32: return rows_lanes<T, 32>(a, split, vec16, grid, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int VEC, int G>
+static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
+  auto kern = merge_kernel<T, VEC, G>;
+  const size_t smem = merge_smem_bytes<T, VEC, G>(threads, a.items);
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<a.ctas, threads, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  merge_fixup_kernel<T><<<(a.ctas + 255) / 256, 256, 0, s>>>(a.ctas, a.k, a.carry_row, a.carry_val, a.Y, a.ldy);
+  return cudaGetLastError();
+}
+
+template <typename T, int G>
+static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, int threads, cudaStream_t s) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if (vec16 && a.k > 1) return merge_go<T, V, G>(a, threads, s);
+  return merge_go<T, 1, G>(a, threads, s);
+}
+
+template <typename T>
+cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
+                           const MergeScratch& S, cudaStream_t s) {
+  if (A.m == 0) return cudaSuccess;
+  MergeArgs<T> a;
+  a.m = A.m;
+  a.k = D.k;
+  a.nnz = A.nnz;
+  a.row_ptr = A.row_ptr;
+  a.col_idx = A.col_idx;
+  a.vals = static_cast<const T*>(A.vals);
+  a.X = static_cast<const T*>(D.X);
+  a.Y = static_cast<T*>(D.Y);
+  a.ldx = D.ldx;
+  a.ldy = D.ldy;
+  a.items = items;
+  a.ctas = S.ctas;
+  a.coords = S.coords;
+  a.carry_row = S.carry_row;
+  a.carry_val = static_cast<T*>(S.carry_val);
+  a.aligned_vals = (reinterpret_cast<uintptr_t>(A.vals) & 15) == 0;
+  a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
+  switch (g) {
+    case 1: return merge_g<T, 1>(a, vec16, threads, s);
+    case 2: return merge_g<T, 2>(a, vec16, threads, s);
+    case 4: return merge_g<T, 4>(a, vec16, threads, s);
+    case 8: return merge_g<T, 8>(a, vec16, threads, s);
+    case 16: return merge_g<T, 16>(a, vec16, threads, s);
+    case 32: return merge_g<T, 32>(a, vec16, threads, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+size_t merge_smem_t(int g, bool vec16, int threads, int items) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const int vec = vec16 ? V : 1;
+  // same formula for every G: s_cval holds threads * vec elements
+  const int nt = threads / g;
+  const size_t ipc = (size_t)nt * items;
+  size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
+  size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
+  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  size_t d = ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;
+  size_t e = (size_t)threads * vec * sizeof(T);
+  return a + b + c + d + e;
+}
+
+}  // namespace gbs

@@ -1,0 +1,257 @@
+// Merge-path CSR kernel ("MERGE" variant) for SpMV and SpMM.
+//
+// Load balance for power-law rows, which the paper's one-row-per-thread
+// kernel (Sec. 4.1) cannot give (webbase-1M has a 4700-nonzero row among
+// 3-nonzero ones, Sec. 4 Table "tab:matrices").  The work is the merge of two
+// sorted lists, the row ends row_ptr[1..m] and the nonzero positions
+// 0..nnz-1 (Merrill & Garland, "Merge-based parallel sparse matrix-vector
+// multiplication", SC'16): every thread takes the same number of items
+// (row ends + nonzeros), whatever the row lengths.
+//
+// GB300-specific choices:
+//   * The inner loop walks the thread's nonzeros and emits the rows that end
+//     between them, so each nonzero costs one fused multiply-add per output
+//     element and row ends cost no FP64 work (GB300's FP64 pipe is the
+//     scarce resource; a masked FP64 instruction costs as much as a full one).
+//   * A row split across threads is finished by the thread where it ends,
+//     which adds the carries of the threads before it in a fixed order (a
+//     short look-back through shared memory) instead of a log-depth scan.
+//   * A row split across CTAs is finished by a separate fix-up pass over the
+//     per-CTA carries, in CTA order.  No atomics: the result is bitwise
+//     reproducible.
+//   * A group of G lanes shares one merge thread; each lane owns VEC of the
+//     k columns (SpMM), so the X row of a nonzero is gathered with G
+//     coalesced 128-bit loads.
+#pragma once
+#include "device_common.cuh"
+
+namespace gbs {
+
+template <typename T>
+struct MergeArgs {
+  int m, k, nnz;
+  const int* __restrict__ row_ptr;
+  const int* __restrict__ col_idx;
+  const T* __restrict__ vals;
+  const T* __restrict__ X;
+  T* __restrict__ Y;
+  long long ldx, ldy;
+  int items;             // merge items per merge thread
+  int ctas;              // number of CTA tiles
+  const int2* __restrict__ coords;  // [ctas + 1] (row, nonzero) at the start of each tile
+  int* __restrict__ carry_row;      // [ctas]
+  T* __restrict__ carry_val;        // [ctas * k]
+  bool aligned_vals, aligned_cols;
+};
+
+// Merge-path search: split diagonal d of the (row ends x nonzeros) grid.
+// Returns (i, d - i): i row ends and d - i nonzeros precede the split.
+// A row end that equals a nonzero position is taken first (that nonzero
+// belongs to a later row).
+__device__ __forceinline__ int2 merge_search_global(const int* __restrict__ row_ptr, int m, int nnz, long long d) {
+  long long lo = d - nnz > 0 ? d - nnz : 0;
+  long long hi = d < m ? d : m;
+  while (lo < hi) {
+    long long mid = (lo + hi) >> 1;
+    if ((long long)__ldg(row_ptr + mid + 1) <= d - 1 - mid)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return make_int2((int)lo, (int)(d - lo));
+}
+
+template <typename T, int VEC, int G>
+__host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
+  int nt = threads / G;
+  size_t ipc = (size_t)nt * items;
+  size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;           // s_rp
+  size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;             // s_val
+  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;           // s_col
+  size_t d = ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;          // s_crow
+  size_t e = (size_t)nt * G * VEC * sizeof(T);                       // s_cval
+  return a + b + c + d + e;
+}
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int nt = blockDim.x / G;
+  const int ipc = nt * a.items;
+  const int2 cs = a.coords[b], ce = a.coords[b + 1];
+  const int row0 = cs.x, nz0 = cs.y, row1 = ce.x, nz1 = ce.y;
+  const long long d0 = (long long)row0 + nz0;
+  const int span = (int)((long long)row1 + nz1 - d0);  // items in this tile
+
+  int* s_rp = reinterpret_cast<int*>(smem_raw);
+  size_t off = (((size_t)ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
+  T* s_val = reinterpret_cast<T*>(smem_raw + off);
+  off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
+  int* s_col = reinterpret_cast<int*>(smem_raw + off);
+  off += (((size_t)ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  int* s_crow = reinterpret_cast<int*>(smem_raw + off);
+  off += ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;
+  T* s_cval = reinterpret_cast<T*>(smem_raw + off);
+
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+
+  // row_ptr window: s_rp[q] = row_ptr[row0 + q] for rows row0 .. min(row1, m-1), plus its end
+  const int rlast = min(row1, a.m - 1);
+  const int nrp = rlast >= row0 ? rlast - row0 + 2 : 0;
+  for (int q = threadIdx.x; q < nrp; q += blockDim.x) s_rp[q] = ld_stream(a.row_ptr + row0 + q, pol_stream);
+  const int a0 = nz0 & ~3;
+  if (nz1 > nz0) {
+    stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
+    stage_copy<int>(s_col, a.col_idx, a0, nz1, a.aligned_cols, pol_stream);
+  }
+  __syncthreads();
+
+  const int t = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const int c_lo = lane * VEC;
+  const bool col_active = c_lo < a.k;
+  const bool col_full = c_lo + VEC <= a.k;
+
+  // this merge thread's share of the tile: diagonals [ds, de) relative to d0
+  const int ds = min(t * a.items, span), de = min(ds + a.items, span);
+  const int wrows = row1 - row0, wnz = nz1 - nz0;
+  auto local_search = [&](int dd) {
+    int lo = max(0, dd - wnz), hi = min(dd, wrows);
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (s_rp[mid + 1] <= nz0 + dd - 1 - mid)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  const int ri_s = local_search(ds), ri_e = local_search(de);
+  const int row_s = row0 + ri_s, nz_s = nz0 + ds - ri_s;
+  const int row_e = row0 + ri_e, nz_e = nz0 + de - ri_e;
+
+  // the thread's first row started before its first nonzero: another thread holds its head
+  const bool head_partial = (row_s < a.m) && (nz_s > s_rp[ri_s]);
+
+  Acc<T> acc[VEC];
+  Acc<T> head[VEC];
+  int head_row = -1;
+  bool first = true;
+  int row = row_s;
+  const T* __restrict__ Xc = a.X + c_lo;
+
+  auto emit = [&](int r) {
+    if (first && head_partial) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) head[j] = acc[j];
+      head_row = r;
+    } else if (col_active) {
+      T* yr = a.Y + (long long)r * a.ldy + c_lo;
+      T out[VEC];
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
+      if (col_full)
+        st_stream_vec<T, VEC>(yr, out);
+      else
+        for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+    }
+    first = false;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) acc[j].reset();
+  };
+
+  constexpr int U = 4;
+  for (int nz = nz_s; nz < nz_e; nz += U) {
+    const int cnt = min(U, nz_e - nz);
+    T v[U];
+    Vec<T, VEC> xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < cnt && col_active) {
+        v[u] = s_val[nz + u - a0];
+        const int c = s_col[nz + u - a0];
+        if (col_full) {
+          xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
+        } else {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) xv[u].v[j] = (c_lo + j < a.k) ? ld_keep(Xc + (long long)c * a.ldx + j, pol_keep) : T(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < cnt) {
+        while (row < row_e && s_rp[row - row0 + 1] <= nz + u) {
+          emit(row);
+          ++row;
+        }
+        if (col_active) {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+        }
+      }
+    }
+  }
+  while (row < row_e) {
+    emit(row);
+    ++row;
+  }
+
+  // carry: the row still open at the end of this thread's share
+  if (lane == 0) s_crow[t] = row_e;
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) s_cval[((size_t)t * G + lane) * VEC + j] = acc[j].value();
+  __syncthreads();
+
+  if (head_row >= 0 && col_active) {
+    // finish the split head row: own part, then the carries of earlier threads in order
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      for (int tp = t - 1; tp >= 0 && s_crow[tp] == head_row; --tp) head[j].add_partial(s_cval[((size_t)tp * G + lane) * VEC + j]);
+    }
+    T* yr = a.Y + (long long)head_row * a.ldy + c_lo;
+    T out[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) out[j] = head[j].value();
+    if (col_full)
+      st_stream_vec<T, VEC>(yr, out);
+    else
+      for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+  }
+
+  if (t == nt - 1) {
+    // CTA carry: sum of the trailing thread carries of the row still open at the tile's end
+    const int crow = s_crow[nt - 1];
+    if (lane == 0) a.carry_row[b] = crow < a.m ? crow : -1;
+    if (col_active) {
+      for (int j = 0; j < VEC && c_lo + j < a.k; ++j) {
+        Acc<T> s;
+        for (int tp = nt - 1; tp >= 0 && s_crow[tp] == crow; --tp) s.add_partial(s_cval[((size_t)tp * G + lane) * VEC + j]);
+        a.carry_val[(size_t)b * a.k + c_lo + j] = s.value();
+      }
+    }
+  }
+}
+
+// Adds the CTA carries to the rows they belong to: the first CTA of each run of
+// equal carry rows sums the run in CTA order and adds it to Y (row finished by a
+// later CTA, which has already written its own part).
+template <typename T>
+__global__ void merge_fixup_kernel(int ctas, int k, const int* __restrict__ carry_row, const T* __restrict__ carry_val,
+                                   T* __restrict__ Y, long long ldy) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ctas) return;
+  const int r = carry_row[b];
+  if (r < 0) return;
+  if (b > 0 && carry_row[b - 1] == r) return;
+  for (int c = 0; c < k; ++c) {
+    Acc<T> s;
+    for (int bb = b; bb < ctas && carry_row[bb] == r; ++bb) s.add_partial(carry_val[(size_t)bb * k + c]);
+    T* yp = Y + (long long)r * ldy + c;
+    *yp = *yp + s.value();
+  }
+}
+
+}  // namespace gbs

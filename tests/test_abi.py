@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function that
+include/*.h declares; argument errors are reported before any CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1302_1078_gb300 import _capi
+
+    return _capi.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("spmv_csr", "spmm_csr", "gbs_plan_create", "spmv_csr_plan", "gbs_validate_csr"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1302_1078_gb300 import _capi
+
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    # and the Python binding declares a signature for each of them
+    unbound = [n for n in declared_functions() if n not in _capi.SIGNATURES]
+    assert not unbound, f"no ctypes signature for: {unbound}"
+
+
+def test_status_strings(lib):
+    assert lib.gbs_status_string(0) == b"ok"
+    assert lib.gbs_status_string(-1) == b"invalid argument"
+    assert lib.gbs_version() >= 100
+
+
+def test_argument_errors_need_no_gpu(lib):
+    from paper_1302_1078_gb300 import _capi
+
+    # negative sizes, bad dtype, ld < k: rejected on the host before any CUDA call
+    assert lib.spmv_csr(-1, 4, 0, None, None, None, 0, None, None, None) == _capi.GBS_EINVAL
+    assert lib.spmv_csr(4, 4, 0, 16, None, None, 7, None, None, None) == _capi.GBS_EDTYPE
+    assert lib.spmm_csr(4, 4, 0, 16, None, None, 0, 8, 16, 4, 16, 8, None) == _capi.GBS_EINVAL
+    assert lib.spmm_csr(4, 4, 0, 16, None, None, 0, 0, 16, 4, 16, 4, None) == _capi.GBS_EINVAL
+    assert lib.spmv_csr(4, 4, 10, 16, None, None, 0, 16, 16, None) == _capi.GBS_EINVAL  # NULL col_idx with nnz > 0
+    assert b"NULL" in lib.gbs_last_error()
+    assert lib.gbs_plan_create(None, 1, 1, 0, None, None, 0, 1, 0, None) == _capi.GBS_EINVAL
+    cfg = _capi.gbs_config(variant=1, lanes=3, threads=256, tile_nnz=2048, items=0)
+    assert lib.spmv_csr_cfg(4, 4, 0, 16, None, None, 0, 16, 16, ctypes.byref(cfg), None) == _capi.GBS_EINVAL
+
+
+def test_default_config_host_only(lib):
+    from paper_1302_1078_gb300 import _capi
+
+    st = _capi.gbs_stats(m=1000, n=1000, nnz=27000, max_row=27, empty_rows=0, mean_row=27.0, cv_row=0.05)
+    c = _capi.gbs_config()
+    assert lib.gbs_default_config(ctypes.byref(st), 0, 1, ctypes.byref(c)) == 0
+    assert c.variant == _capi.VARIANT_ROWS and c.lanes == 1
+    st2 = _capi.gbs_stats(m=1000, n=1000, nnz=16000, max_row=5000, empty_rows=300, mean_row=16.0, cv_row=8.0)
+    assert lib.gbs_default_config(ctypes.byref(st2), 0, 1, ctypes.byref(c)) == 0
+    assert c.variant == _capi.VARIANT_MERGE

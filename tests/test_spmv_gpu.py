@@ -1,0 +1,254 @@
+"""Parity of the CUDA SpMV / SpMM path (through the C ABI) with the CPU oracle.
+
+Bound (per output entry): |y_gpu - y_oracle| <= tol * sum_p |a_p x_p|, with
+tol = 1e-12 for FP64 and 2e-5 for FP32 inputs; an entry whose bound is 0 must
+be exactly 0.  Index-valued facts (closed forms with integer results,
+permutations) must match bitwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+NP = {torch.float64: np.float64, torch.float32: np.float32}
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    import paper_1302_1078_gb300 as g
+
+    g.lib()
+    return g
+
+
+def dev_csr(A: synth.CSR, dtype=torch.float64):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(A.row_ptr).to(d), torch.from_numpy(A.col_idx).to(d),
+            torch.from_numpy(A.vals.astype(NP[dtype])).to(d))
+
+
+def assert_close(y_gpu, y_ref, r, dtype, what=""):
+    y = y_gpu.double().cpu().numpy().reshape(y_ref.shape)
+    err = np.abs(y - y_ref)
+    tol = TOL[dtype]
+    bad = err > tol * r
+    if bad.any():
+        i = np.argwhere(bad)[0]
+        raise AssertionError(f"{what}: {bad.sum()} entries off; first {tuple(i)}: gpu {y[tuple(i)]!r} "
+                             f"oracle {y_ref[tuple(i)]!r} bound {tol * r[tuple(i)]!r}")
+    zero = r == 0
+    assert np.all(y[zero] == 0.0), f"{what}: entries with zero bound are not exactly 0"
+
+
+def spmv_ref(A, x, dtype):
+    v = A.vals.astype(NP[dtype])
+    return oracle.spmv(A.m, A.row_ptr, A.col_idx, v, x.astype(NP[dtype]))
+
+
+def hub_matrix():
+    """Empty rows around one 100k-nonzero row and a few short ones."""
+    m, n = 64, 200000
+    lens = np.zeros(m, np.int64)
+    lens[5] = 100000
+    lens[6:12] = 3
+    lens[40] = 7000
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rng = np.random.default_rng(5)
+    ci = np.concatenate([np.sort(rng.choice(n, int(l), replace=False)) for l in lens if l > 0]).astype(np.int32)
+    v = rng.uniform(-1, 1, ci.size)
+    return synth.CSR(m, n, rp.astype(np.int32), ci, v, "hub")
+
+
+MATRICES = {
+    "stencil2d_64": lambda: synth.stencil2d(64),
+    "stencil2d_37": lambda: synth.stencil2d(37),
+    "stencil3d_21": lambda: synth.stencil3d(21),
+    "banded_30k": lambda: synth.banded(30001, hbw=1000, per_row=50, seed=3),
+    "rmat_14": lambda: synth.rmat(14, ef=16, seed=4),
+    "random_rect": lambda: synth.random_csr(333, 1201, 0.02, 5, empty_rows=0.3),
+    "random_dup_unsorted": lambda: synth.random_csr(257, 257, 0.05, 6, sorted_cols=False, duplicates=True),
+    "empty_nnz": lambda: synth.random_csr(100, 50, 0.0, 7),
+    "one_row": lambda: synth.random_csr(1, 5000, 0.5, 8),
+    "hub": hub_matrix,
+}
+
+_cache = {}
+
+
+def matrix(name):
+    if name not in _cache:
+        _cache[name] = MATRICES[name]()
+    return _cache[name]
+
+
+CONFIGS = [None,
+           dict(variant=1, lanes=1), dict(variant=1, lanes=2), dict(variant=1, lanes=4), dict(variant=1, lanes=8),
+           dict(variant=1, lanes=16), dict(variant=1, lanes=32),
+           dict(variant=1, lanes=1, threads=64, tile_nnz=64), dict(variant=1, lanes=4, threads=128, tile_nnz=100),
+           dict(variant=2, items=1), dict(variant=2, items=4), dict(variant=2, items=16, threads=64),
+           dict(variant=2, items=7, threads=96)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_spmv_parity_all_variants(gbs, name, dtype):
+    A = matrix(name)
+    x = synth.uniform(A.n, seed=synth.BASE_SEED, stream=11)
+    y_ref, r = spmv_ref(A, x, dtype)
+    rp, ci, v = dev_csr(A, dtype)
+    xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+    for cfg in CONFIGS:
+        y = torch.full((A.m,), float("nan"), dtype=dtype, device="cuda")
+        gbs.spmv_csr(rp, ci, v, xd, y, config=cfg)
+        assert_close(y, y_ref, r, dtype, f"{name} {cfg}")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 8, 16, 33, 70])
+@pytest.mark.parametrize("name", ["stencil2d_37", "banded_30k", "rmat_14", "random_rect", "hub", "empty_nnz"])
+def test_spmm_parity(gbs, name, k, dtype):
+    A = matrix(name)
+    if name == "hub" and k > 16:
+        pytest.skip("covered by smaller k")
+    rng = np.random.default_rng(k)
+    ld = k + 3  # row stride > k: exercises the narrow-access path
+    Xw = synth.uniform(A.n * ld, seed=synth.BASE_SEED, stream=100 + k).reshape(A.n, ld).astype(NP[dtype])
+    X = Xw[:, :k]
+    Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), X)
+    rp, ci, v = dev_csr(A, dtype)
+    Xd_wide = torch.from_numpy(Xw).cuda()
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    for cfg in [None, dict(variant=1), dict(variant=1, threads=128, tile_nnz=500), dict(variant=2),
+                dict(variant=2, items=3, threads=128)]:
+        for XX in (Xd, Xd_wide[:, :k]):
+            Y = torch.full((A.m, k), float("nan"), dtype=dtype, device="cuda")
+            gbs.spmm_csr(rp, ci, v, XX, Y, config=cfg)
+            assert_close(Y, Y_ref, R, dtype, f"{name} k={k} {cfg} ld={XX.stride(0)}")
+    del rng
+
+
+def test_stencil_closed_forms_bitwise(gbs):
+    N = 50
+    A = synth.stencil2d(N)
+    rp, ci, v = dev_csr(A)
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    miss = ((i == 0).astype(int) + (i == N - 1) + (j == 0) + (j == N - 1)).reshape(-1).astype(float)
+    for cfg in CONFIGS:
+        y = gbs.spmv_csr(rp, ci, v, torch.ones(A.n, dtype=torch.float64, device="cuda"), config=cfg)
+        assert np.array_equal(y.cpu().numpy(), miss), cfg
+
+
+def test_permutation_bitwise(gbs):
+    rng = np.random.default_rng(3)
+    m = 100003
+    pi = rng.permutation(m).astype(np.int32)
+    rp = torch.arange(m + 1, dtype=torch.int32, device="cuda")
+    ci = torch.from_numpy(pi).cuda()
+    v = torch.ones(m, dtype=torch.float64, device="cuda")
+    x = torch.from_numpy(rng.uniform(-1, 1, m)).cuda()
+    for cfg in CONFIGS:
+        y = gbs.spmv_csr(rp, ci, v, x, config=cfg)
+        assert torch.equal(y, x[ci.long()]), cfg
+
+
+def test_determinism_bitwise(gbs):
+    A = matrix("rmat_14")
+    rp, ci, v = dev_csr(A)
+    x = torch.from_numpy(synth.uniform(A.n, seed=1)).cuda()
+    for cfg in CONFIGS:
+        y1 = gbs.spmv_csr(rp, ci, v, x, config=cfg)
+        y2 = gbs.spmv_csr(rp, ci, v, x, config=cfg)
+        assert torch.equal(y1, y2), cfg
+
+
+@pytest.mark.parametrize("k", [1, 8])
+def test_plans_and_tuner(gbs, k):
+    for name in ("stencil3d_21", "rmat_14", "hub"):
+        A = matrix(name)
+        rp, ci, v = dev_csr(A)
+        plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True, check=True)
+        st = plan.stats
+        lens = A.row_lengths()
+        assert st["max_row"] == lens.max() and st["empty_rows"] == int((lens == 0).sum())
+        assert st["nnz"] == A.nnz and st["m"] == A.m
+        if k == 1:
+            x = synth.uniform(A.n, seed=2)
+            y_ref, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+            y = plan.spmv(v, torch.from_numpy(x).cuda())
+            assert_close(y, y_ref, r, torch.float64, f"plan {name} {plan.config}")
+        else:
+            X = synth.uniform(A.n * k, seed=3).reshape(A.n, k)
+            Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals, X)
+            Y = plan.spmm(v, torch.from_numpy(X).cuda())
+            assert_close(Y, Y_ref, R, torch.float64, f"plan {name} {plan.config}")
+        # every other configuration through the same plan
+        for cfg in (dict(variant=1, lanes=2), dict(variant=2, items=5)):
+            plan.set_config(cfg)
+            if k == 1:
+                assert_close(plan.spmv(v, torch.from_numpy(x).cuda()), y_ref, r, torch.float64, f"{name} {cfg}")
+            else:
+                assert_close(plan.spmm(v, torch.from_numpy(X).cuda()), Y_ref, R, torch.float64, f"{name} {cfg}")
+
+
+def test_stats_and_validation(gbs):
+    from paper_1302_1078_gb300 import _capi
+
+    A = matrix("random_rect")
+    rp, ci, v = dev_csr(A)
+    st = gbs.csr_stats(rp, A.n)
+    lens = A.row_lengths()
+    assert st["max_row"] == lens.max() and st["empty_rows"] == int((lens == 0).sum())
+    assert st["rows_over_32"] == int((lens > 32).sum())
+    assert abs(st["mean_row"] - lens.mean()) < 1e-12
+    assert abs(st["cv_row"] - lens.std() / lens.mean()) < 1e-9
+    gbs.validate_csr(rp, ci, A.n)
+    bad = ci.clone()
+    bad[3] = A.n  # one column id out of range (only validated, never multiplied)
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.validate_csr(rp, bad, A.n)
+    assert e.value.status == _capi.GBS_EINDEX
+    rp_bad = rp.clone()
+    rp_bad[0] = 1
+    with pytest.raises(gbs.GbsError):
+        gbs.validate_csr(rp_bad, ci, A.n)
+
+
+def test_zero_rows_and_zero_columns(gbs):
+    rp = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v = torch.zeros(0, dtype=torch.float64, device="cuda")
+    y = gbs.spmv_csr(rp, ci, v, torch.zeros(10, dtype=torch.float64, device="cuda"))
+    assert y.numel() == 0
+    # n = 0: all rows empty
+    rp = torch.zeros(6, dtype=torch.int32, device="cuda")
+    y = gbs.spmv_csr(rp, ci, v, torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert torch.equal(y, torch.zeros(5, dtype=torch.float64, device="cuda"))
+
+
+# ------------------------------------------------ full-size configurations
+
+FULL = {
+    "stencil3d_100": lambda: synth.stencil3d(100),
+    "banded_2M": lambda: synth.banded(2_000_000, hbw=1000, per_row=50, seed=synth.BASE_SEED + 1),
+    "rmat_22": lambda: synth.rmat(22, ef=16, seed=synth.BASE_SEED + 1),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_spmv_tuned_plan(gbs, name):
+    """The bench's matrices and launch path (tuned plan), every row checked."""
+    A = FULL[name]()
+    x = synth.uniform(A.n, seed=synth.BASE_SEED + 1, stream=1)
+    y_ref, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x, threads=oracle.max_threads())
+    rp, ci, v = dev_csr(A)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, 1, tune=True)
+    y = plan.spmv(v, torch.from_numpy(x).cuda())
+    assert_close(y, y_ref, r, torch.float64, f"{name} {plan.config}")
+    y2 = gbs.spmv_csr(rp, ci, v, torch.from_numpy(x).cuda())
+    assert_close(y2, y_ref, r, torch.float64, f"{name} auto")
