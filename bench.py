@@ -308,6 +308,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     sampler.start()
     time.sleep(0.05)
+    torch.cuda.nvtx.range_push("timed")
     t0 = time.perf_counter()
     for s in range(args.steps):
         flush.zero_()
@@ -317,6 +318,7 @@ def run_gpu(args, rank, world, local_rank):
             ev[s][j][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     sampler.stop()

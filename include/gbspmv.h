@@ -188,6 +188,43 @@ int spmv_csr_plan(const gbs_plan* plan, const void* vals, const void* x, void* y
 int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx, void* Y, int ldy,
                   void* stream);
 
+/* ---------------------------------------------------- transpose + backward */
+/*
+ * CSR of A^T (n x m), i.e. the CCS of A (Sec. 3: the two formats are dual),
+ * built on the device by a stable sort of the nonzeros by column: inside a
+ * row of A^T the entries keep their order of storage in A, so the result is
+ * unique and bit-exact (no atomics decide any position).  The plan owns
+ *   rowptrT[n+1], colT[nnz] (row of A of each entry), perm[nnz] (position in
+ *   A of each entry of A^T), the row of every nonzero of A, and nnz doubles
+ *   of scratch for the permuted values.
+ * It does not keep row_ptr / col_idx.  Synchronises `stream`.
+ * The transpose is the one-time set-up of the backward pass.
+ */
+typedef struct gbs_tplan gbs_tplan;
+
+int gbs_transpose_plan(gbs_tplan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx,
+                       void* stream);
+/* Device pointers owned by the plan (any output may be NULL). */
+int gbs_tplan_arrays(const gbs_tplan* plan, const int** rowptrT, const int** colT, const int** perm);
+/* Copy the plan's arrays into caller buffers (device or host, cudaMemcpyDefault), async on `stream`. */
+int gbs_tplan_export(const gbs_tplan* plan, int* rowptrT, int* colT, int* perm, void* stream);
+int gbs_tplan_destroy(gbs_tplan* plan);
+
+/*
+ * Backward of Y = A X (k >= 1 columns; k == 1 is SpMV) for a loss L with
+ * upstream gradient dY = dL/dY (m x k, ld lddy):
+ *   dX[j, c] = sum_{p : col_idx[p] = j} vals[p] * dY[row(p), c]   i.e. dX = A^T dY
+ *   dvals[p] = sum_c dY[row(p), c] * X[col_idx[p], c]             (sampled dense-dense product)
+ * dX (n x k, ld lddx) and dvals (nnz) may each be NULL to skip that output.
+ * dX runs the forward kernels on A^T (values permuted into the plan's
+ * scratch, so calls that share a plan must be ordered on one stream); dvals
+ * sums each nonzero's k products in column order.  `plan` must come from
+ * gbs_transpose_plan on the same (row_ptr, col_idx); row_ptr is unused.
+ */
+int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                      int k, const void* X, int ldx, const void* dY, int lddy, void* dX, int lddx, void* dvals,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ from ._capi import GbsError, gbs_config, gbs_stats  # noqa: F401
 
 __all__ = [
     "spmv_csr", "spmm_csr", "Plan", "csr_stats", "validate_csr", "default_config", "GbsError", "lib",
+    "TransposePlan", "CsrOperator", "SpMMFunction", "spmm_autograd",
 ]
 
 
@@ -221,3 +222,119 @@ class Plan:
         _capi.check(lib().spmm_csr_plan(self._h, _ptr(vals), _ptr(X), max(X.stride(0), self.k), _ptr(Y),
                                         max(Y.stride(0), self.k), _stream(self.device, stream)), "spmm_csr_plan")
         return Y
+
+
+# --------------------------------------------------------- transpose + backward
+
+class TransposePlan:
+    """CSR of A^T built on the device (stable, bit-exact) plus the backward kernels."""
+
+    def __init__(self, row_ptr, col_idx, n: int, stream=None):
+        _check_index(row_ptr, col_idx)
+        dev = _need_cuda(row_ptr, col_idx)
+        self.row_ptr, self.col_idx = row_ptr, col_idx
+        self.m, self.n, self.nnz = row_ptr.numel() - 1, int(n), col_idx.numel()
+        self.device = dev
+        self._h = ctypes.c_void_p()
+        _capi.check(lib().gbs_transpose_plan(ctypes.byref(self._h), self.m, self.n, self.nnz, _ptr(row_ptr),
+                                             _ptr(col_idx), _stream(dev, stream)), "gbs_transpose_plan")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().gbs_tplan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def arrays(self, stream=None):
+        """(row_ptr_T [n+1], col_idx_T [nnz], perm [nnz]) as new int32 device tensors."""
+        rpT = torch.empty(self.n + 1, dtype=torch.int32, device=self.device)
+        ciT = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        perm = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        _capi.check(lib().gbs_tplan_export(self._h, _ptr(rpT), _ptr(ciT), _ptr(perm), _stream(self.device, stream)),
+                    "gbs_tplan_export")
+        return rpT, ciT, perm
+
+    def backward(self, vals, X, dY, need_dX: bool = True, need_dvals: bool = True, stream=None):
+        """(dX, dvals) of Y = A X for upstream dY; X and dY are 1-D (SpMV) or 2-D row major."""
+        _need_cuda(vals, X, dY)
+        dt = _dtype_code(vals)
+        vec = X.dim() == 1
+        k = 1 if vec else X.shape[1]
+        if X.dtype != vals.dtype or dY.dtype != vals.dtype:
+            raise TypeError("X and dY must have the values' dtype")
+        if vec:
+            X2, dY2 = X.contiguous(), dY.contiguous()
+            ldx = lddy = 1
+        else:
+            X2 = X if X.stride(1) == 1 else X.contiguous()
+            dY2 = dY if dY.stride(1) == 1 else dY.contiguous()
+            ldx, lddy = max(X2.stride(0), k), max(dY2.stride(0), k)
+        dX = None
+        if need_dX:
+            dX = torch.empty(self.n if vec else (self.n, k), dtype=vals.dtype, device=self.device)
+        dvals = torch.empty(self.nnz, dtype=vals.dtype, device=self.device) if need_dvals else None
+        _capi.check(lib().spmv_csr_backward(self._h, _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(vals), dt, k,
+                                            _ptr(X2), ldx, _ptr(dY2), lddy, _ptr(dX), k, _ptr(dvals),
+                                            _stream(self.device, stream)), "spmv_csr_backward")
+        return dX, dvals
+
+
+class CsrOperator:
+    """A fixed sparsity pattern A (m x n) whose product with X is differentiable in both the
+    stored values and X:  Y = op(vals, X).  Forward runs through plans (one per k), backward
+    through a TransposePlan built on first use (the one-time transpose)."""
+
+    def __init__(self, row_ptr, col_idx, n: int, tune: bool = False):
+        _check_index(row_ptr, col_idx)
+        self.row_ptr, self.col_idx, self.n = row_ptr, col_idx, int(n)
+        self.m = row_ptr.numel() - 1
+        self.tune = tune
+        self._plans = {}
+        self._tplan = None
+
+    def plan(self, dtype, k):
+        key = (dtype, k)
+        if key not in self._plans:
+            self._plans[key] = Plan(self.row_ptr, self.col_idx, self.n, dtype, k, tune=self.tune)
+        return self._plans[key]
+
+    @property
+    def tplan(self) -> TransposePlan:
+        if self._tplan is None:
+            self._tplan = TransposePlan(self.row_ptr, self.col_idx, self.n)
+        return self._tplan
+
+    def forward_raw(self, vals, X):
+        if X.dim() == 1:
+            return self.plan(vals.dtype, 1).spmv(vals, X.contiguous())
+        Xc = X if X.stride(1) == 1 else X.contiguous()
+        return self.plan(vals.dtype, X.shape[1]).spmm(vals, Xc)
+
+    def __call__(self, vals, X):
+        return SpMMFunction.apply(vals, X, self)
+
+
+class SpMMFunction(torch.autograd.Function):
+    """Y = A X (or y = A x) with gradients for the stored values and for X."""
+
+    @staticmethod
+    def forward(ctx, vals, X, op: CsrOperator):
+        ctx.op = op
+        ctx.save_for_backward(vals, X)
+        return op.forward_raw(vals, X)
+
+    @staticmethod
+    def backward(ctx, dY):
+        vals, X = ctx.saved_tensors
+        need_v, need_x = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        dX, dvals = ctx.op.tplan.backward(vals, X, dY, need_dX=need_x, need_dvals=need_v)
+        return dvals, dX, None
+
+
+def spmm_autograd(row_ptr, col_idx, vals, X, n: int | None = None):
+    """One-shot differentiable product (builds a CsrOperator; reuse one for repeated calls)."""
+    n = X.shape[0] if n is None else n
+    return CsrOperator(row_ptr, col_idx, n)(vals, X)

@@ -74,6 +74,11 @@ SIGNATURES = {
     "gbs_plan_get_stats": (I32, [P, ctypes.POINTER(gbs_stats)]),
     "spmv_csr_plan": (I32, [P, P, P, P, P]),
     "spmm_csr_plan": (I32, [P, P, P, I32, P, I32, P]),
+    "gbs_transpose_plan": (I32, [ctypes.POINTER(P), I32, I32, I32, P, P, P]),
+    "gbs_tplan_arrays": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
+    "gbs_tplan_export": (I32, [P, P, P, P, P]),
+    "gbs_tplan_destroy": (I32, [P]),
+    "spmv_csr_backward": (I32, [P, P, P, P, I32, I32, P, I32, P, I32, P, I32, P, P]),
 }
 
 

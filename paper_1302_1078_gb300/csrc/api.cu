@@ -710,3 +710,146 @@ int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx
 }
 
 }  // extern "C"
+
+// ======================================================= transpose + backward
+
+struct gbs_tplan {
+  int m = 0, n = 0, nnz = 0, device = 0;
+  int* rptrT = nullptr;  // n + 1
+  int* colT = nullptr;   // nnz
+  int* perm = nullptr;   // nnz
+  int* rows = nullptr;   // nnz: row of every nonzero of A
+  void* valsT = nullptr; // nnz doubles (scratch for the permuted values)
+  void* base = nullptr;
+  gbs_stats statsT{};
+};
+
+namespace {
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" {
+
+int gbs_transpose_plan(gbs_tplan** out, int m, int n, int nnz, const int* row_ptr, const int* col_idx, void* stream) {
+  if (!out) return fail(GBS_EINVAL, "plan is NULL");
+  *out = nullptr;
+  int rc = check_csr(m, n, nnz, row_ptr, col_idx, reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (checked_mode()) {
+    rc = gbs_validate_csr(m, n, nnz, row_ptr, col_idx, stream);
+    if (rc) return rc;
+  }
+  gbs_tplan* t = new (std::nothrow) gbs_tplan();
+  if (!t) return fail(GBS_ENOMEM, "host allocation");
+  t->m = m;
+  t->n = n;
+  t->nnz = nnz;
+  cudaGetDevice(&t->device);
+  const size_t z = (size_t)std::max(nnz, 1);
+  size_t b_rptr = align256(sizeof(int) * ((size_t)n + 1)), b_i = align256(sizeof(int) * z), b_v = align256(8 * z);
+  size_t keep = b_rptr + 3 * b_i + b_v;
+  size_t b_hist = align256(sizeof(int) * transpose_hist_ints(nnz));
+  size_t b_scan = align256(sizeof(int) * transpose_scan_ws_ints(nnz));
+  size_t tmp = 4 * b_i + b_hist + b_scan;
+  cudaError_t e = cudaMalloc(&t->base, keep);
+  if (e != cudaSuccess) {
+    delete t;
+    return cuda_fail(e, "cudaMalloc (transpose plan)");
+  }
+  char* p = static_cast<char*>(t->base);
+  t->rptrT = reinterpret_cast<int*>(p);
+  p += b_rptr;
+  t->colT = reinterpret_cast<int*>(p);
+  p += b_i;
+  t->perm = reinterpret_cast<int*>(p);
+  p += b_i;
+  t->rows = reinterpret_cast<int*>(p);
+  p += b_i;
+  t->valsT = p;
+  void* work = nullptr;
+  e = cudaMallocAsync(&work, tmp, s);
+  if (e == cudaSuccess) {
+    char* w = static_cast<char*>(work);
+    int* ka = reinterpret_cast<int*>(w);
+    int* kb = reinterpret_cast<int*>(w + b_i);
+    int* va = reinterpret_cast<int*>(w + 2 * b_i);
+    int* vb = reinterpret_cast<int*>(w + 3 * b_i);
+    int* hist = reinterpret_cast<int*>(w + 4 * b_i);
+    int* ws = reinterpret_cast<int*>(w + 4 * b_i + b_hist);
+    e = transpose_run(m, n, nnz, row_ptr, col_idx, t->rptrT, t->colT, t->perm, t->rows, ka, kb, va, vb, hist, ws, s);
+    cudaError_t e2 = cudaFreeAsync(work, s);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(t->base);
+    delete t;
+    return cuda_fail(e, "transpose");
+  }
+  rc = compute_stats(n, m, nnz, t->rptrT, &t->statsT, s);
+  if (rc) {
+    cudaFree(t->base);
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return GBS_OK;
+}
+
+int gbs_tplan_arrays(const gbs_tplan* t, const int** rowptrT, const int** colT, const int** perm) {
+  if (!t) return fail(GBS_EINVAL, "plan is NULL");
+  if (rowptrT) *rowptrT = t->rptrT;
+  if (colT) *colT = t->colT;
+  if (perm) *perm = t->perm;
+  return GBS_OK;
+}
+
+int gbs_tplan_export(const gbs_tplan* t, int* rowptrT, int* colT, int* perm, void* stream) {
+  if (!t) return fail(GBS_EINVAL, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (rowptrT) e = cudaMemcpyAsync(rowptrT, t->rptrT, sizeof(int) * ((size_t)t->n + 1), cudaMemcpyDefault, s);
+  if (e == cudaSuccess && colT && t->nnz)
+    e = cudaMemcpyAsync(colT, t->colT, sizeof(int) * (size_t)t->nnz, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && perm && t->nnz)
+    e = cudaMemcpyAsync(perm, t->perm, sizeof(int) * (size_t)t->nnz, cudaMemcpyDefault, s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "tplan export");
+}
+
+int gbs_tplan_destroy(gbs_tplan* t) {
+  if (!t) return GBS_OK;
+  if (t->base) cudaFree(t->base);
+  delete t;
+  return GBS_OK;
+}
+
+int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, const void* vals, int dtype, int k,
+                      const void* X, int ldx, const void* dY, int lddy, void* dX, int lddx, void* dvals,
+                      void* stream) {
+  if (!t) return fail(GBS_EINVAL, "plan is NULL");
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (k < 1 || ldx < k || lddy < k || (dX && lddx < k)) return fail(GBS_EINVAL, "k or leading dimension");
+  if (t->nnz > 0 && (!col_idx || !vals)) return fail(GBS_EINVAL, "col_idx or vals is NULL");
+  if (dvals && t->nnz > 0 && (!X || !dY)) return fail(GBS_EINVAL, "X or dY is NULL");
+  if (dX && t->m > 0 && !dY) return fail(GBS_EINVAL, "dY is NULL");
+  (void)row_ptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (dX) {
+    // dX = A^T dY through the precomputed transpose: values permuted once per call
+    e = gather_values(dtype, vals, t->perm, t->nnz, t->valsT, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gather of A^T values");
+    CsrView AT{t->n, t->m, t->nnz, t->rptrT, t->colT, t->valsT};
+    gbs_config c = heuristic_config(t->statsT, dtype, k);
+    int rc = run_product(AT, dtype, k, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, c, nullptr, false, s);
+    if (rc) return rc;
+  }
+  if (dvals) {
+    e = launch_sddmm(dtype, t->nnz, k, t->rows, col_idx, X, k == 1 ? 1 : ldx, dY, k == 1 ? 1 : lddy, dvals, s);
+    if (e != cudaSuccess) return cuda_fail(e, "SDDMM launch");
+  }
+  return GBS_OK;
+}
+
+}  // extern "C"

@@ -44,6 +44,24 @@ cudaError_t launch_merge_f32(const CsrView& A, const DenseView& D, int g, bool v
                              const MergeScratch& S, cudaStream_t s);
 cudaError_t launch_merge_partition(const CsrView& A, long long items_per_cta, const MergeScratch& S, cudaStream_t s);
 
+// Exclusive prefix sum of int32 (in == out allowed); ws holds scan_workspace_ints(count) ints.
+cudaError_t exclusive_scan_i32(const int* in, int* out, long long count, int* ws, cudaStream_t s);
+size_t scan_workspace_ints(long long count);
+
+// Transpose (transpose.cu).  Buffer sizes: rptrT n+1, colT/perm/rows/keys_a/keys_b/vals_a/vals_b nnz,
+// hist transpose_hist_ints(nnz), scan_ws transpose_scan_ws_ints(nnz).
+cudaError_t transpose_run(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int* rptrT, int* colT,
+                          int* perm, int* rows, int* keys_a, int* keys_b, int* vals_a, int* vals_b, int* hist,
+                          int* scan_ws, cudaStream_t s);
+size_t transpose_hist_ints(int nnz);
+size_t transpose_scan_ws_ints(int nnz);
+// out[q] = src[perm[q]] for values of `dtype`.
+cudaError_t gather_values(int dtype, const void* src, const int* perm, int nnz, void* out, cudaStream_t s);
+
+// dvals[p] = sum_c dY[rows[p], c] * X[col_idx[p], c]  (backward.cu)
+cudaError_t launch_sddmm(int dtype, int nnz, int k, const int* rows, const int* col_idx, const void* X, long long ldx,
+                         const void* dY, long long lddy, void* dvals, cudaStream_t s);
+
 // Shared-memory bytes of one CTA (host helpers).
 size_t rows_smem(int dtype, int rows_per_cta, int tile);
 size_t merge_smem(int dtype, int g, bool vec16, int threads, int items);

@@ -1,0 +1,185 @@
+"""Transpose (bit-exact) and backward (dX = A^T dY, dvals) of the CUDA path against the
+CPU oracle, plus central finite differences through the autograd Function."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+NP = {torch.float64: np.float64, torch.float32: np.float32}
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    import paper_1302_1078_gb300 as g
+
+    g.lib()
+    return g
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def within(got, ref, bound, dtype, what):
+    g = got.double().cpu().numpy().reshape(ref.shape)
+    bad = np.abs(g - ref) > TOL[dtype] * bound
+    assert not bad.any(), f"{what}: {bad.sum()} entries off, e.g. {g[bad][:3]} vs {ref[bad][:3]}"
+    assert np.all(g[bound == 0] == 0), f"{what}: nonzero where the bound is 0"
+
+
+CASES = {
+    "random_rect": lambda: synth.random_csr(300, 170, 0.05, 1, empty_rows=0.2),
+    "random_tall": lambda: synth.random_csr(170, 300, 0.05, 2, empty_rows=0.2),
+    "dup_unsorted": lambda: synth.random_csr(200, 200, 0.05, 3, sorted_cols=False, duplicates=True),
+    "stencil2d_37": lambda: synth.stencil2d(37),
+    "banded_20k": lambda: synth.banded(20000, hbw=1000, per_row=30, seed=4),
+    "rmat_14": lambda: synth.rmat(14, ef=16, seed=5, vals="u0.5_1.5"),
+    "one_col": lambda: synth.CSR(5000, 1, np.arange(5001, dtype=np.int32), np.zeros(5000, np.int32),
+                                 np.linspace(-1, 1, 5000)),
+    "empty": lambda: synth.random_csr(50, 60, 0.0, 6),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        _cache[name] = CASES[name]()
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_transpose_bit_exact(gbs, name):
+    A = case(name)
+    rpT, ciT, perm = oracle.transpose(A.m, A.n, A.row_ptr, A.col_idx)
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    g_rpT, g_ciT, g_perm = (x.cpu().numpy() for x in t.arrays())
+    assert np.array_equal(g_rpT, rpT)
+    assert np.array_equal(g_ciT, ciT)
+    assert np.array_equal(g_perm, perm)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8, 16])
+@pytest.mark.parametrize("name", list(CASES))
+def test_backward_matches_oracle(gbs, name, k, dtype):
+    A = case(name)
+    v = A.vals.astype(NP[dtype])
+    X = synth.uniform(A.n * k, seed=11, stream=k).reshape(A.n, k).astype(NP[dtype])
+    W = synth.uniform(A.m * k, seed=12, stream=k).reshape(A.m, k).astype(NP[dtype])
+    dX_ref, dv_ref, RdX, Rdv = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, v, X, W)
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    vd = dev(v)
+    if k == 1:
+        dX, dvals = t.backward(vd, dev(X[:, 0]), dev(W[:, 0]))
+    else:
+        dX, dvals = t.backward(vd, dev(X), dev(W))
+    within(dX, dX_ref, RdX, dtype, f"dX {name} k={k}")
+    within(dvals, dv_ref, Rdv, dtype, f"dvals {name} k={k}")
+    # determinism
+    dX2, dvals2 = t.backward(vd, dev(X) if k > 1 else dev(X[:, 0]), dev(W) if k > 1 else dev(W[:, 0]))
+    assert torch.equal(dX, dX2) and torch.equal(dvals, dvals2)
+
+
+def test_autograd_gradcheck(gbs):
+    A = synth.random_csr(12, 9, 0.3, 21, empty_rows=0.2)
+    op = gbs.CsrOperator(dev(A.row_ptr), dev(A.col_idx), A.n)
+    vals = dev(A.vals).requires_grad_(True)
+    X = torch.rand(A.n, 3, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda v, x: op(v, x), (vals, X), eps=1e-6, atol=1e-9, rtol=1e-7)
+    x1 = torch.rand(A.n, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda v, x: op(v, x), (vals, x1), eps=1e-6, atol=1e-9, rtol=1e-7)
+
+
+def fd_checks(gbs, A, k, dtype=torch.float64, h=1e-6, ndir=8, ncoord=64, seed=0):
+    """Central differences of L(vals, X) = <A X, W> against the autograd gradients.  L is bilinear,
+    so the differences are exact up to rounding; they are formed entry by entry
+    ((Y+ - Y-) . W) so that the unchanged entries cancel exactly."""
+    rng = np.random.default_rng(seed)
+    op = gbs.CsrOperator(dev(A.row_ptr), dev(A.col_idx), A.n)
+    v0 = dev(A.vals.astype(NP[dtype]))
+    X0 = dev(synth.uniform(A.n * k, seed=31, stream=k).reshape(A.n, k).astype(NP[dtype])).squeeze(1) if k == 1 else \
+        dev(synth.uniform(A.n * k, seed=31, stream=k).reshape(A.n, k).astype(NP[dtype]))
+    W = dev(synth.uniform(A.m * k, seed=32, stream=k).astype(NP[dtype]))
+    W = W if k == 1 else W.reshape(A.m, k)
+    vals = v0.clone().requires_grad_(True)
+    X = X0.clone().requires_grad_(True)
+    L = (op(vals, X) * W).sum()
+    gv, gx = torch.autograd.grad(L, (vals, X))
+
+    def fd(dv, dx):
+        Yp = op.forward_raw(v0 + h * dv, X0 + h * dx)
+        Ym = op.forward_raw(v0 - h * dv, X0 - h * dx)
+        return float(((Yp - Ym) * W).sum()) / (2 * h)
+
+    for _ in range(ndir):
+        dv = dev(rng.uniform(-1, 1, A.nnz))
+        dx = dev(rng.uniform(-1, 1, tuple(X0.shape)))
+        zero_v, zero_x = torch.zeros_like(dv), torch.zeros_like(dx)
+        assert fd(dv, zero_x) == pytest.approx(float((gv * dv).sum()), rel=1e-7, abs=1e-8)
+        assert fd(zero_v, dx) == pytest.approx(float((gx * dx).sum()), rel=1e-7, abs=1e-8)
+    for _ in range(ncoord):
+        p = int(rng.integers(A.nnz))
+        e = torch.zeros(A.nnz, dtype=dtype, device="cuda")
+        e[p] = 1
+        assert fd(e, torch.zeros_like(X0)) == pytest.approx(float(gv[p]), rel=1e-7, abs=1e-9)
+        j = int(rng.integers(A.n))
+        ex = torch.zeros_like(X0)
+        if k == 1:
+            ex[j] = 1
+            g = float(gx[j])
+        else:
+            c = int(rng.integers(k))
+            ex[j, c] = 1
+            g = float(gx[j, c])
+        assert fd(torch.zeros_like(v0), ex) == pytest.approx(g, rel=1e-7, abs=1e-9)
+    return gv, gx
+
+
+@pytest.mark.parametrize("k", [1, 8])
+def test_finite_differences_small(gbs, k):
+    fd_checks(gbs, case("rmat_14"), k, ndir=4, ncoord=16)
+
+
+# ----------------------------------------- full size: R-MAT scale 20, edge factor 16
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return synth.rmat(20, ef=16, seed=synth.BASE_SEED + 3, vals="u0.5_1.5")
+
+
+def test_full_transpose_rmat20(gbs, rmat20):
+    A = rmat20
+    rpT, ciT, perm = oracle.transpose(A.m, A.n, A.row_ptr, A.col_idx)
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    g = [x.cpu().numpy() for x in t.arrays()]
+    assert np.array_equal(g[0], rpT) and np.array_equal(g[1], ciT) and np.array_equal(g[2], perm)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 8])
+def test_full_backward_rmat20(gbs, rmat20, k, dtype):
+    A = rmat20
+    v = A.vals.astype(NP[dtype])
+    X = synth.uniform(A.n * k, seed=41, stream=k).reshape(A.n, k).astype(NP[dtype])
+    W = synth.uniform(A.m * k, seed=42, stream=k).reshape(A.m, k).astype(NP[dtype])
+    dX_ref, dv_ref, RdX, Rdv = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, v, X, W)
+    op = gbs.CsrOperator(dev(A.row_ptr), dev(A.col_idx), A.n)
+    vals = dev(v).requires_grad_(True)
+    Xd = (dev(X[:, 0]) if k == 1 else dev(X)).requires_grad_(True)
+    Wd = dev(W[:, 0]) if k == 1 else dev(W)
+    Y = op(vals, Xd)
+    Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, v, X)
+    within(Y, Y_ref, R, dtype, "forward")
+    gv, gx = torch.autograd.grad((Y * Wd).sum(), (vals, Xd))
+    within(gx, dX_ref, RdX, dtype, "dX")
+    within(gv, dv_ref, Rdv, dtype, "dvals")
+
+
+@pytest.mark.parametrize("k", [1, 8])
+def test_full_finite_differences_rmat20(gbs, rmat20, k):
+    fd_checks(gbs, rmat20, k, ndir=8, ncoord=64, seed=k)
