@@ -66,6 +66,11 @@ WORKLOAD_TEXT = {
     "spmm": "FP64 CSR SpMM Y=A X, X row-major n x k, k in {1,4,8,16}, on the 27-pt 100^3, banded 2M and "
             "R-MAT 22 matrices; X uniform[-1,1]",
     "small": "FP64 CSR SpMV, 2D 5-pt Laplacian 64x64 (m=4096, nnz=20,224)",
+    "batched": "Batched FP64 SpMM, 512 CSR matrices (rows log-uniform 1k-200k, avg nnz/row 4-64, round-robin "
+               "2D stencil / random banded / R-MAT), k=8 right-hand sides uniform[-1,1], one persistent launch "
+               "replayed from a CUDA graph, per-matrix autotuned configuration",
+    "autograd": "Differentiable SpMV/SpMM on R-MAT scale 20 ef 16, vals uniform[0.5,1.5], k in {1,8}, FP64 and "
+                "FP32: forward Y=A X, backward dX=A^T dY and dvals (transpose built once, timed separately)",
 }
 
 
@@ -415,14 +420,188 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+# --------------------------------------------------------------- batched mode
+
+def shard_for_rank(costs, world: int, rank: int):
+    """Indices of the batch members rank `rank` multiplies: greedy longest-processing-time
+    assignment of the costs to `world` ranks (deterministic: ties broken by index)."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    owner = [0] * len(costs)
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += costs[i]
+    return [i for i in range(len(costs)) if owner[i] == rank]
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    k = 8
+    if args.shard:
+        # one batch split across the ranks (strong scaling)
+        specs = synth.batch_specs(512)
+        costs = [sp.rows * (5 if sp.kind == "stencil2d" else sp.avg) for sp in specs]
+        mine = shard_for_rank(costs, world, rank)
+    else:
+        # every rank its own independent batch (weak scaling)
+        specs = synth.batch_specs(512, seed=synth.BASE_SEED + 4 + 1000 * rank)
+        mine = list(range(len(specs)))
+    mats, Xs, Ys, flops, bytes_ = [], [], [], 0.0, 0
+    for i in mine:
+        A = synth.batch_matrix(specs[i])
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col_idx).to(dev)
+        v = torch.from_numpy(A.vals).to(dev)
+        X = torch.from_numpy(synth.uniform(A.n * k, seed=synth.BASE_SEED + 4, stream=i).reshape(A.n, k)).to(dev)
+        mats.append((rp, ci, v, A.n))
+        Xs.append(X)
+        Ys.append(torch.empty((A.m, k), dtype=torch.float64, device=dev))
+        flops += 2.0 * A.nnz * k
+        bytes_ += compulsory_bytes(A.m, A.n, A.nnz, k)
+    plan = gbs.BatchedPlan(mats, Xs, Ys, tune=True)
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s_ in range(steps):
+            flush.zero_()
+            evs[s_][0].record(stream)
+            fn()
+            evs[s_][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    for _ in range(args.warmup):
+        plan.run()
+        plan.run_looped()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_smi_id(torch, local_rank))
+    if world > 1:
+        dist.barrier()
+    sampler.start()
+    time.sleep(0.05)
+    torch.cuda.nvtx.range_push("timed")
+    t_batched = timed(plan.run, args.steps)
+    torch.cuda.nvtx.range_pop()
+    t_looped = timed(plan.run_looped, args.steps)
+    sampler.stop()
+    ms_b, ms_l = statistics.mean(t_batched), statistics.mean(t_looped)
+    t = torch.tensor([ms_b, ms_l], dtype=torch.float64, device=dev)
+    tot = torch.tensor([flops, float(bytes_)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_b, ms_l = float(t[0]), float(t[1])
+    flops_all, bytes_all = float(tot[0]), float(tot[1])
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    variants = {}
+    for c in info["configs"]:
+        key = "ROWS" if c["variant"] == 1 else "MERGE"
+        variants[key] = variants.get(key, 0) + 1
+    line = {
+        "metric": METRIC, "value": flops_all / (ms_b * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["batched"], "matrices_per_rank": len(mine),
+                   "grid": info["grid"], "work_items": info["total_items"], "variants": variants,
+                   "l2": "256 MiB write before every step (untimed)"},
+        "batched_vs_looped": ms_l / ms_b, "looped_gflops": flops_all / (ms_l * 1e-3) / 1e9,
+        "looped_ms": ms_l,
+        "roofline": {"bound": "hbm", "achieved": bytes_all / (ms_b * 1e-3) / 1e9 / world, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": bytes_all / (ms_b * 1e-3) / 1e9 / world / hbm_peak, "traffic": None,
+                     "kernel": "batched_kernel (whole batch per launch)"},
+        "clocks": sampler.summary(),
+        "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------ autograd
+
+def run_autograd(args, rank, world, local_rank):
+    import torch
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    A = synth.rmat(20, ef=16, seed=synth.BASE_SEED + 3 + 1000 * rank, vals="u0.5_1.5")
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = gbs.CsrOperator(rp, ci, A.n, tune=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    op.tplan  # the one-time transpose
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    transpose_ms = e0.elapsed_time(e1)
+    results = []
+    for dtype in (torch.float64, torch.float32):
+        v = torch.from_numpy(A.vals).to(dev).to(dtype)
+        for k in (1, 8):
+            X = torch.from_numpy(synth.uniform(A.n * k, seed=5, stream=k)).to(dev).to(dtype)
+            X = X if k == 1 else X.reshape(A.n, k)
+            W = torch.rand((A.m,) if k == 1 else (A.m, k), dtype=dtype, device=dev)
+            op.forward_raw(v, X)
+            for _ in range(args.warmup):
+                op.forward_raw(v, X)
+                op.tplan.backward(v, X, W)
+            torch.cuda.synchronize(dev)
+            fwd, bwd = [], []
+            for _ in range(args.steps):
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                op.forward_raw(v, X)
+                b.record(stream)
+                op.tplan.backward(v, X, W)
+                c.record(stream)
+                fwd.append((a, b))
+                bwd.append((b, c))
+            torch.cuda.synchronize(dev)
+            f = statistics.mean(x.elapsed_time(y) for x, y in fwd)
+            bw = statistics.mean(x.elapsed_time(y) for x, y in bwd)
+            results.append({"dtype": str(dtype).replace("torch.", ""), "k": k, "fwd_ms": f, "bwd_ms": bw,
+                            "bwd_over_fwd": bw / f, "fwd_gflops": 2.0 * A.nnz * k / (f * 1e-3) / 1e9,
+                            "bwd_gflops": 4.0 * A.nnz * k / (bw * 1e-3) / 1e9})
+    main_r = results[0]
+    line = {
+        "metric": METRIC, "value": main_r["fwd_gflops"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_r["fwd_ms"] + main_r["bwd_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["autograd"], "m": A.m, "nnz": A.nnz},
+        "transpose_ms_one_time": transpose_ms, "autograd": results,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small"])
+    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd"])
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -433,6 +612,10 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world, local_rank)
+    if args.workload == "autograd":
+        return run_autograd(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

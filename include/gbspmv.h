@@ -225,6 +225,62 @@ int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, c
                       int k, const void* X, int ldx, const void* dY, int lddy, void* dX, int lddx, void* dvals,
                       void* stream);
 
+/* ---------------------------------------------------------------- batched */
+/*
+ * Many independent products Y_b <- A_b X_b (b < nmat; k columns for all, k
+ * == 1 is SpMV), each the product of Sec. 3 / Sec. 5, run by one persistent
+ * kernel replayed from a CUDA graph.  The plan
+ *   - picks each matrix's configuration (ROWS lanes / tile or MERGE items;
+ *     256 threads) from its row statistics, or with GBS_PLAN_TUNE by timing
+ *     candidates with standalone launches on the given operands (this
+ *     writes Y_b);
+ *   - builds the work list: matrix b owns the contiguous items
+ *     [item_begin[b], item_begin[b+1]) (row blocks or merge tiles), and
+ *     item i is processed by CTA i mod grid, grid = every resident CTA slot;
+ *   - owns a device descriptor table, the merge scratch and the graph.
+ * The arrays of every item must stay valid and unchanged while the plan is
+ * used (only X and Y may be replaced, below).  Results equal
+ * spmv_csr_batched_looped (one standalone launch per matrix with the same
+ * configuration) bitwise.  Plan creation synchronises `stream`.
+ * k must fit one column panel (k <= 64 for FP64 / 128 for FP32 with 16-byte
+ * aligned X/Y rows, else k <= 32).
+ */
+typedef struct {
+  int m, n, nnz;
+  const int* row_ptr;
+  const int* col_idx;
+  const void* vals;
+  const void* X; /* n x k, row major, leading dimension ldx (ignored for k == 1) */
+  int ldx;
+  void* Y;       /* m x k, row major, leading dimension ldy (ignored for k == 1) */
+  int ldy;
+} gbs_batch_item;
+
+typedef struct gbs_batch_plan gbs_batch_plan;
+
+int spmv_csr_batched_plan(gbs_batch_plan** plan, int nmat, const gbs_batch_item* items /* host */, int dtype,
+                          int k, int flags, void* stream);
+/*
+ * Launch the captured graph on `stream`.  X and Y (host arrays of nmat device
+ * pointers, or NULL to keep the current ones) replace the dense operands
+ * first; they must keep the shapes and the 16-byte alignment class of plan
+ * time.  Replacing them synchronises `stream`.
+ */
+int spmv_csr_batched(gbs_batch_plan* plan, const void* const* X, void* const* Y, void* stream);
+/* The same products as a host loop of per-matrix launches (no graph): the baseline. */
+int spmv_csr_batched_looped(gbs_batch_plan* plan, void* stream);
+/* Host copies: cfgs[nmat], item_begin[nmat+1], grid, total work items (any may be NULL). */
+int spmv_csr_batched_info(const gbs_batch_plan* plan, gbs_config* cfgs, int* item_begin, int* grid,
+                          int* total_items);
+/*
+ * Offsets of each matrix in concatenated batch buffers (host arrays of nmat+1,
+ * exclusive prefix sums in input order): rows, nonzeros, row_ptr entries (m+1
+ * each), X entries (n*k) and Y entries (m*k).  Any may be NULL.
+ */
+int spmv_csr_batched_offsets(const gbs_batch_plan* plan, long long* off_rows, long long* off_nnz,
+                             long long* off_rptr, long long* off_x, long long* off_y);
+int spmv_csr_batched_destroy(gbs_batch_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

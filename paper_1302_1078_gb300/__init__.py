@@ -21,7 +21,7 @@ from ._capi import GbsError, gbs_config, gbs_stats  # noqa: F401
 
 __all__ = [
     "spmv_csr", "spmm_csr", "Plan", "csr_stats", "validate_csr", "default_config", "GbsError", "lib",
-    "TransposePlan", "CsrOperator", "SpMMFunction", "spmm_autograd",
+    "TransposePlan", "CsrOperator", "SpMMFunction", "spmm_autograd", "BatchedPlan",
 ]
 
 
@@ -338,3 +338,83 @@ def spmm_autograd(row_ptr, col_idx, vals, X, n: int | None = None):
     """One-shot differentiable product (builds a CsrOperator; reuse one for repeated calls)."""
     n = X.shape[0] if n is None else n
     return CsrOperator(row_ptr, col_idx, n)(vals, X)
+
+
+# ---------------------------------------------------------------------- batched
+
+class BatchedPlan:
+    """Many products Y_b = A_b X_b in one persistent launch replayed from a CUDA graph.
+
+    ``mats``: list of (row_ptr, col_idx, vals, n); ``X``/``Y``: lists of dense operands
+    (1-D for k == 1, else n x k / m x k row major).  Keeps references to every tensor."""
+
+    def __init__(self, mats, X, Y, *, tune: bool = False, check: bool = False, stream=None):
+        if not (len(mats) == len(X) == len(Y)) or not mats:
+            raise ValueError("mats, X and Y must be non-empty lists of equal length")
+        self.nmat = len(mats)
+        self.dtype = mats[0][2].dtype
+        self.k = 1 if X[0].dim() == 1 else X[0].shape[1]
+        dev = _need_cuda(*[t for mat in mats for t in mat[:3]], *X, *Y)
+        self.device = dev
+        self._keep = (list(mats), list(X), list(Y))
+        arr = (_capi.gbs_batch_item * self.nmat)()
+        for b, ((rp, ci, v, n), x, y) in enumerate(zip(mats, X, Y)):
+            _check_index(rp, ci)
+            if v.dtype != self.dtype or x.dtype != self.dtype or y.dtype != self.dtype:
+                raise TypeError("all values and operands must share one dtype")
+            kk = 1 if x.dim() == 1 else x.shape[1]
+            if kk != self.k:
+                raise ValueError("every X must have the same k")
+            it = arr[b]
+            it.m, it.n, it.nnz = rp.numel() - 1, int(n), ci.numel()
+            it.row_ptr, it.col_idx, it.vals = _ptr(rp), _ptr(ci), _ptr(v)
+            it.X, it.Y = _ptr(x), _ptr(y)
+            it.ldx = max(x.stride(0), self.k) if x.dim() == 2 else 1
+            it.ldy = max(y.stride(0), self.k) if y.dim() == 2 else 1
+        self._items = arr
+        self._h = ctypes.c_void_p()
+        flags = (_capi.PLAN_TUNE if tune else 0) | (_capi.PLAN_CHECK if check else 0)
+        _capi.check(lib().spmv_csr_batched_plan(ctypes.byref(self._h), self.nmat, arr, _dtype_code(mats[0][2]),
+                                                self.k, flags, _stream(dev, stream)), "spmv_csr_batched_plan")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().spmv_csr_batched_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def run(self, X=None, Y=None, stream=None):
+        """Replay the graph (optionally with new X / Y lists of the same shapes)."""
+        xp = yp = None
+        if X is not None:
+            xp = (ctypes.c_void_p * self.nmat)(*[_ptr(t) for t in X])
+            self._keep = (self._keep[0], list(X), self._keep[2])
+        if Y is not None:
+            yp = (ctypes.c_void_p * self.nmat)(*[_ptr(t) for t in Y])
+            self._keep = (self._keep[0], self._keep[1], list(Y))
+        _capi.check(lib().spmv_csr_batched(self._h, xp, yp, _stream(self.device, stream)), "spmv_csr_batched")
+
+    def run_looped(self, stream=None):
+        """The same products as one launch per matrix (the baseline)."""
+        _capi.check(lib().spmv_csr_batched_looped(self._h, _stream(self.device, stream)), "spmv_csr_batched_looped")
+
+    def info(self) -> dict:
+        cfgs = (gbs_config * self.nmat)()
+        ib = (ctypes.c_int * (self.nmat + 1))()
+        grid, total = ctypes.c_int(), ctypes.c_int()
+        _capi.check(lib().spmv_csr_batched_info(self._h, cfgs, ib, ctypes.byref(grid), ctypes.byref(total)),
+                    "spmv_csr_batched_info")
+        return {"configs": [c.as_dict() for c in cfgs], "item_begin": list(ib), "grid": grid.value,
+                "total_items": total.value}
+
+    def offsets(self):
+        """(rows, nonzeros, row_ptr entries, X entries, Y entries) offsets, each nmat + 1 int64."""
+        import numpy as np
+
+        outs = [np.zeros(self.nmat + 1, np.int64) for _ in range(5)]
+        ptrs = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) for o in outs]
+        _capi.check(lib().spmv_csr_batched_offsets(self._h, *ptrs), "spmv_csr_batched_offsets")
+        return tuple(outs)

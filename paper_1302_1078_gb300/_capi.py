@@ -115,3 +115,20 @@ class GbsError(RuntimeError):
 def check(status: int, where: str) -> None:
     if status != GBS_OK:
         raise GbsError(status, where)
+
+
+class gbs_batch_item(ctypes.Structure):
+    _fields_ = [("m", I32), ("n", I32), ("nnz", I32), ("row_ptr", P), ("col_idx", P), ("vals", P),
+                ("X", P), ("ldx", I32), ("Y", P), ("ldy", I32)]
+
+
+SIGNATURES.update({
+    "spmv_csr_batched_plan": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(gbs_batch_item), I32, I32, I32, P]),
+    "spmv_csr_batched": (I32, [P, P, P, P]),
+    "spmv_csr_batched_looped": (I32, [P, P]),
+    "spmv_csr_batched_info": (I32, [P, ctypes.POINTER(gbs_config), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                    ctypes.POINTER(I32)]),
+    "spmv_csr_batched_offsets": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                       ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    "spmv_csr_batched_destroy": (I32, [P]),
+})

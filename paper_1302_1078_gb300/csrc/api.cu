@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "batched.cuh"
 #include "gbspmv.h"
 #include "launch.h"
 #include "merge_kernel.cuh"
@@ -70,7 +71,13 @@ bool dense_vec16(int dtype, int k, const void* X, long long ldx, const void* Y, 
   return aligned16(X) && aligned16(Y) && ((ldx * (long long)es) % 16 == 0) && ((ldy * (long long)es) % 16 == 0);
 }
 
-int default_items(int g, int threads) { return std::max(4, (2048 * g) / threads); }
+// Items per merge thread: about 3840 items per CTA, an odd count so that the merge threads'
+// contiguous segments in shared memory start in different banks.
+int default_items(int g, int threads) {
+  int it = std::max(5, (3840 * g) / threads);
+  if (it % 2 == 0) --it;
+  return std::min(it, 255);
+}
 
 gbs_config normalize(const gbs_config& c, int dtype) {
   gbs_config r = c;
@@ -93,8 +100,8 @@ int check_cfg(const gbs_config& c) {
   if (c.threads % 32 != 0 || c.threads < 32 || c.threads > 1024) return fail(GBS_EINVAL, "threads must be 32..1024, multiple of 32");
   if (c.variant == GBS_VARIANT_MERGE && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
   if (c.lanes != 0 && !pow2_lanes(c.lanes)) return fail(GBS_EINVAL, "lanes must be 1, 2, 4, 8, 16 or 32");
-  if (c.variant == GBS_VARIANT_ROWS && (c.tile_nnz < 32 || c.tile_nnz > (1 << 16)))
-    return fail(GBS_EINVAL, "tile_nnz must be in [32, 65536]");
+  if (c.variant == GBS_VARIANT_ROWS && (c.tile_nnz < 32 || c.tile_nnz > (1 << 14)))
+    return fail(GBS_EINVAL, "tile_nnz must be in [32, 16384]");
   if (c.variant == GBS_VARIANT_MERGE && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
   return GBS_OK;
 }
@@ -330,6 +337,9 @@ __global__ void fp64_probe_kernel(double* __restrict__ out, int iters) {
 }  // namespace
 
 namespace gbs {
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+
 // Start coordinates of every merge-path tile: one thread per tile boundary.
 __global__ void merge_partition_kernel(const int* __restrict__ row_ptr, int m, int nnz, int ctas,
                                        long long items_per_cta, int2* __restrict__ coords) {
@@ -552,14 +562,22 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     c.push_back(normalize(g, p->dtype));
   };
   const int base_tile = p->dtype == GBS_F64 ? 2048 : 3072;
+  // a tile that holds a whole row block in the common case: rows per CTA x mean row length
+  auto fit_tile = [&](int threads, int lanes) {
+    double want = (double)(threads / lanes) * p->stats.mean_row * 1.1 + 64;
+    int t = 1024;
+    while (t < want && t < 16384) t <<= 1;
+    return t;
+  };
   if (p->k == 1) {
     for (int l : {1, 2, 4, 8, 16, 32}) {
       if (l > 1 && p->stats.mean_row < 0.5 * l) continue;
       add(GBS_VARIANT_ROWS, l, 256, base_tile, 0);
+      if (fit_tile(256, l) != base_tile) add(GBS_VARIANT_ROWS, l, 256, fit_tile(256, l), 0);
     }
-    add(GBS_VARIANT_ROWS, 1, 128, base_tile, 0);
-    add(GBS_VARIANT_ROWS, 1, 256, base_tile * 2, 0);
-    for (int it : {4, 8, 16}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
+    add(GBS_VARIANT_ROWS, 1, 128, fit_tile(128, 1), 0);
+    add(GBS_VARIANT_ROWS, 2, 128, fit_tile(128, 2), 0);
+    for (int it : {7, 11, 15, 23, 31}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
@@ -849,6 +867,369 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
     e = launch_sddmm(dtype, t->nnz, k, t->rows, col_idx, X, k == 1 ? 1 : ldx, dY, k == 1 ? 1 : lddy, dvals, s);
     if (e != cudaSuccess) return cuda_fail(e, "SDDMM launch");
   }
+  return GBS_OK;
+}
+
+}  // extern "C"
+
+// ================================================================== batched
+
+struct gbs_batch_plan {
+  int nmat = 0, dtype = GBS_F64, k = 1, device = 0;
+  bool split = true, vec16 = false;
+  int G = 1;
+  std::vector<gbs_batch_item> items;
+  std::vector<gbs_config> cfgs;
+  std::vector<int> item_begin;  // nmat + 1
+  std::vector<MergeBuffers> mbs;
+  std::vector<unsigned char> h_desc;
+  void* d_desc = nullptr;
+  void* scratch = nullptr;
+  size_t smem = 0;
+  int grid = 0, total_items = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+
+size_t rows_smem_host(int dtype, int rpc, int tile) {
+  return dtype == GBS_F64 ? rows_smem_bytes<double>(rpc, tile) : rows_smem_bytes<float>(rpc, tile);
+}
+size_t merge_smem_host(int dtype, int g, bool vec16, int items) {
+  const int vec = vec16 ? vec_of(dtype) : 1;
+  const int nt = kBatchThreads / g;
+  const size_t es = dsize(dtype);
+  const size_t ipc = (size_t)nt * items;
+  size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
+  size_t b = ((ipc + 4) * es + 15) & ~(size_t)15;
+  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  return a + b + c + 2 * 32 * sizeof(int) + 2 * (size_t)kBatchThreads * vec * es;
+}
+
+template <typename T>
+void fill_desc(gbs_batch_plan* p, int b, BatchDesc<T>* d) {
+  const gbs_batch_item& it = p->items[b];
+  const gbs_config& c = p->cfgs[b];
+  std::memset(d, 0, sizeof(*d));
+  d->m = it.m;
+  d->n = it.n;
+  d->nnz = it.nnz;
+  d->k = p->k;
+  d->row_ptr = it.row_ptr;
+  d->col_idx = it.col_idx;
+  d->vals = static_cast<const T*>(it.vals);
+  d->X = static_cast<const T*>(it.X);
+  d->Y = static_cast<T*>(it.Y);
+  d->ldx = p->k == 1 ? 1 : it.ldx;
+  d->ldy = p->k == 1 ? 1 : it.ldy;
+  d->variant = c.variant;
+  d->lanes = p->split ? c.lanes : p->G;
+  d->tile = c.tile_nnz;
+  d->items = c.items;
+  d->item_begin = p->item_begin[b];
+  d->nitems = p->item_begin[b + 1] - p->item_begin[b];
+  if (c.variant == GBS_VARIANT_MERGE) {
+    d->coords = p->mbs[b].s.coords;
+    d->carry_row = p->mbs[b].s.carry_row;
+    d->carry_val = static_cast<T*>(p->mbs[b].s.carry_val);
+    d->done = reinterpret_cast<int*>(static_cast<char*>(p->mbs[b].base) + p->mbs[b].bytes - sizeof(int));
+  }
+  d->aligned_vals = aligned16(it.vals);
+  d->aligned_cols = aligned16(it.col_idx);
+}
+
+void batch_free(gbs_batch_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->d_desc) cudaFree(p->d_desc);
+  if (p->scratch) cudaFree(p->scratch);
+  delete p;
+}
+
+// Per-matrix configuration for the batch: 256 threads; k > 1 uses the plan's column lanes.
+std::vector<gbs_config> batch_candidates(const gbs_stats& st, int dtype, int k) {
+  std::vector<gbs_config> c;
+  const int base_tile = dtype == GBS_F64 ? 2048 : 3072;
+  auto add = [&](int variant, int lanes, int tile, int items) {
+    gbs_config g{};
+    g.variant = variant;
+    g.lanes = lanes;
+    g.threads = kBatchThreads;
+    g.tile_nnz = tile;
+    g.items = items;
+    c.push_back(g);
+  };
+  if (k == 1) {
+    for (int l : {1, 2, 4, 8, 16, 32})
+      if (l == 1 || st.mean_row >= 0.5 * l) add(GBS_VARIANT_ROWS, l, base_tile, 0);
+    for (int it : {7, 15, 31}) add(GBS_VARIANT_MERGE, 0, 0, it);
+  } else {
+    add(GBS_VARIANT_ROWS, 0, base_tile, 0);
+    add(GBS_VARIANT_ROWS, 0, base_tile / 2, 0);
+    add(GBS_VARIANT_MERGE, 0, 0, 0);
+  }
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* items, int dtype, int k, int flags,
+                          void* stream) {
+  if (!out) return fail(GBS_EINVAL, "plan is NULL");
+  *out = nullptr;
+  if (nmat < 1 || !items) return fail(GBS_EINVAL, "nmat must be >= 1 and items non-NULL");
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t es = dsize(dtype);
+  bool vec16 = k > 1;
+  for (int b = 0; b < nmat; ++b) {
+    const gbs_batch_item& it = items[b];
+    int rc = check_csr(it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals);
+    if (rc) return fail(rc, "item " + std::to_string(b) + ": " + g_err);
+    if (k > 1 && (it.ldx < k || it.ldy < k)) return fail(GBS_EINVAL, "item " + std::to_string(b) + ": ld < k");
+    if ((it.m > 0 && !it.Y) || (it.nnz > 0 && !it.X)) return fail(GBS_EINVAL, "item " + std::to_string(b) + ": NULL X/Y");
+    if (k > 1) vec16 = vec16 && dense_vec16(dtype, k, it.X, it.ldx, it.Y, it.ldy);
+    if ((reinterpret_cast<uintptr_t>(it.vals) % es) || (reinterpret_cast<uintptr_t>(it.X) % es) ||
+        (reinterpret_cast<uintptr_t>(it.Y) % es))
+      return fail(GBS_EALIGN, "item " + std::to_string(b) + ": arrays must be aligned to their element size");
+    if ((flags & GBS_PLAN_CHECK) || checked_mode()) {
+      rc = gbs_validate_csr(it.m, it.n, it.nnz, it.row_ptr, it.col_idx, stream);
+      if (rc) return fail(rc, "item " + std::to_string(b) + ": " + g_err);
+    }
+  }
+  if (k > panel_cols(dtype, vec16)) return fail(GBS_EUNSUPPORTED, "batched k wider than one column panel (32 lanes)");
+  gbs_batch_plan* p = new (std::nothrow) gbs_batch_plan();
+  if (!p) return fail(GBS_ENOMEM, "host allocation");
+  p->nmat = nmat;
+  p->dtype = dtype;
+  p->k = k;
+  p->split = k == 1;
+  p->vec16 = vec16;
+  p->G = k == 1 ? 1 : col_lanes(k, dtype, vec16);
+  cudaGetDevice(&p->device);
+  p->items.assign(items, items + nmat);
+  p->cfgs.resize(nmat);
+  p->mbs.resize(nmat);
+
+  // ---- per-matrix configuration (heuristic, or timed with standalone launches)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  const bool tune = (flags & GBS_PLAN_TUNE) != 0;
+  if (tune) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+  }
+  for (int b = 0; b < nmat; ++b) {
+    const gbs_batch_item& it = p->items[b];
+    gbs_stats st;
+    int rc = compute_stats(it.m, it.n, it.nnz, it.row_ptr, &st, s);
+    if (rc) {
+      batch_free(p);
+      return rc;
+    }
+    gbs_config c = heuristic_config(st, dtype, k);
+    c.threads = kBatchThreads;
+    if (c.variant == GBS_VARIANT_ROWS && k > 1) c.lanes = p->G;
+    if (tune && it.m > 0) {
+      float best = 1e30f;
+      for (gbs_config cand : batch_candidates(st, dtype, k)) {
+        if (k > 1 && cand.variant == GBS_VARIANT_ROWS) cand.lanes = p->G;
+        CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
+        float ms_sum = 0;
+        bool ok = true;
+        for (int r = 0; r < 3 && ok; ++r) {
+          ok = cudaEventRecord(ev0, s) == cudaSuccess &&
+               run_product(A, dtype, k, it.X, k == 1 ? 1 : it.ldx, it.Y, k == 1 ? 1 : it.ldy, cand, nullptr, false, s) ==
+                   GBS_OK &&
+               cudaEventRecord(ev1, s) == cudaSuccess && cudaEventSynchronize(ev1) == cudaSuccess;
+          float ms = 0;
+          if (ok && r > 0) {
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            ms_sum += ms;
+          }
+        }
+        if (ok && ms_sum < best) {
+          best = ms_sum;
+          c = cand;
+        }
+      }
+    }
+    p->cfgs[b] = c;
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  g_err.clear();
+
+  // ---- work list, shared memory, merge scratch
+  p->item_begin.assign(nmat + 1, 0);
+  size_t scratch_total = 0;
+  std::vector<size_t> scratch_off(nmat, 0);
+  for (int b = 0; b < nmat; ++b) {
+    const gbs_batch_item& it = p->items[b];
+    const gbs_config& c = p->cfgs[b];
+    long long nitems = 0;
+    if (c.variant == GBS_VARIANT_ROWS) {
+      const int lanes = k == 1 ? c.lanes : p->G;
+      const int rpc = kBatchThreads / lanes;
+      nitems = (it.m + rpc - 1) / rpc;
+      p->smem = std::max(p->smem, rows_smem_host(dtype, rpc, c.tile_nnz));
+    } else {
+      const MergeGeom G = merge_geom(c, it.m, it.nnz, dtype, k, vec16);
+      p->cfgs[b].items = G.items;
+      nitems = it.m > 0 ? G.ctas : 0;
+      p->smem = std::max(p->smem, merge_smem_host(dtype, G.g, vec16, G.items));
+      scratch_off[b] = scratch_total;
+      const size_t bytes = align256(merge_scratch_bytes(G.ctas, G.kp_max, dtype) + sizeof(int));
+      p->mbs[b].bytes = bytes;
+      scratch_total += bytes;
+    }
+    if ((long long)p->item_begin[b] + nitems > 0x7fffffffLL) {
+      batch_free(p);
+      return fail(GBS_EUNSUPPORTED, "batch work list exceeds 2^31 items");
+    }
+    p->item_begin[b + 1] = p->item_begin[b] + (int)nitems;
+  }
+  p->total_items = p->item_begin[nmat];
+  cudaError_t e = cudaSuccess;
+  if (scratch_total) {
+    e = cudaMalloc(&p->scratch, scratch_total);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, scratch_total, s);
+    for (int b = 0; b < nmat && e == cudaSuccess; ++b) {
+      if (p->cfgs[b].variant != GBS_VARIANT_MERGE) continue;
+      const gbs_batch_item& it = p->items[b];
+      const MergeGeom G = merge_geom(p->cfgs[b], it.m, it.nnz, dtype, k, vec16);
+      p->mbs[b].base = static_cast<char*>(p->scratch) + scratch_off[b];
+      merge_carve(p->mbs[b], G.ctas, G.kp_max, dtype);
+      if (it.m > 0) {
+        CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
+        e = launch_merge_partition(A, (long long)(kBatchThreads / G.g) * G.items, p->mbs[b].s, s);
+      }
+    }
+  }
+  // ---- descriptors
+  const size_t dsz = dtype == GBS_F64 ? sizeof(BatchDesc<double>) : sizeof(BatchDesc<float>);
+  p->h_desc.assign(dsz * nmat, 0);
+  for (int b = 0; b < nmat; ++b) {
+    if (dtype == GBS_F64)
+      fill_desc<double>(p, b, reinterpret_cast<BatchDesc<double>*>(p->h_desc.data() + dsz * b));
+    else
+      fill_desc<float>(p, b, reinterpret_cast<BatchDesc<float>*>(p->h_desc.data() + dsz * b));
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, p->h_desc.size());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_desc, p->h_desc.data(), p->h_desc.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // ---- persistent grid: every resident CTA slot of the GPU
+  int bps = 0, sms = 0;
+  if (e == cudaSuccess) e = batched_kernel_call(false, dtype, p->split, p->G, vec16, nullptr, 0, 0, 0, p->smem, &bps, s);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    batch_free(p);
+    return cuda_fail(e, "batched plan");
+  }
+  p->grid = std::max(1, std::min(p->total_items, std::max(1, bps) * sms));
+  // ---- capture the launch in a CUDA graph
+  if (p->total_items > 0) {
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = batched_kernel_call(true, dtype, p->split, p->G, vec16, p->d_desc, nmat, p->total_items, p->grid,
+                                           p->smem, nullptr, cs);
+      e = cudaStreamEndCapture(cs, &p->graph);
+      if (el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      batch_free(p);
+      return cuda_fail(e, "batched graph capture");
+    }
+  }
+  *out = p;
+  return GBS_OK;
+}
+
+int spmv_csr_batched(gbs_batch_plan* p, const void* const* X, void* const* Y, void* stream) {
+  if (!p) return fail(GBS_EINVAL, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (X || Y) {
+    // new dense operands: same shapes and alignment class as at plan time
+    const size_t dsz = p->dtype == GBS_F64 ? sizeof(BatchDesc<double>) : sizeof(BatchDesc<float>);
+    for (int b = 0; b < p->nmat; ++b) {
+      if (X) p->items[b].X = X[b];
+      if (Y) p->items[b].Y = Y[b];
+      const gbs_batch_item& it = p->items[b];
+      if ((it.m > 0 && !it.Y) || (it.nnz > 0 && !it.X)) return fail(GBS_EINVAL, "NULL X/Y");
+      if (p->k > 1 && p->vec16 && !dense_vec16(p->dtype, p->k, it.X, it.ldx, it.Y, it.ldy))
+        return fail(GBS_EALIGN, "X/Y lost the 16-byte alignment the plan was made for");
+      if (p->dtype == GBS_F64)
+        fill_desc<double>(p, b, reinterpret_cast<BatchDesc<double>*>(p->h_desc.data() + dsz * b));
+      else
+        fill_desc<float>(p, b, reinterpret_cast<BatchDesc<float>*>(p->h_desc.data() + dsz * b));
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_desc, p->h_desc.data(), p->h_desc.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host table may change again after return
+    if (e != cudaSuccess) return cuda_fail(e, "descriptor update");
+  }
+  if (!p->exec) return GBS_OK;
+  cudaError_t e = cudaGraphLaunch(p->exec, s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int spmv_csr_batched_looped(gbs_batch_plan* p, void* stream) {
+  if (!p) return fail(GBS_EINVAL, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int b = 0; b < p->nmat; ++b) {
+    const gbs_batch_item& it = p->items[b];
+    if (it.m == 0) continue;
+    CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
+    gbs_config c = p->cfgs[b];
+    if (c.variant == GBS_VARIANT_ROWS && p->k > 1) c.lanes = p->G;
+    MergeBuffers mb = p->mbs[b];
+    int rc = run_product(A, p->dtype, p->k, it.X, p->k == 1 ? 1 : it.ldx, it.Y, p->k == 1 ? 1 : it.ldy, c,
+                         c.variant == GBS_VARIANT_MERGE ? &mb : nullptr, true, s);
+    if (rc) return rc;
+  }
+  return GBS_OK;
+}
+
+int spmv_csr_batched_info(const gbs_batch_plan* p, gbs_config* cfgs, int* item_begin, int* grid, int* total_items) {
+  if (!p) return fail(GBS_EINVAL, "plan is NULL");
+  if (cfgs) std::copy(p->cfgs.begin(), p->cfgs.end(), cfgs);
+  if (item_begin) std::copy(p->item_begin.begin(), p->item_begin.end(), item_begin);
+  if (grid) *grid = p->grid;
+  if (total_items) *total_items = p->total_items;
+  return GBS_OK;
+}
+
+int spmv_csr_batched_offsets(const gbs_batch_plan* p, long long* off_rows, long long* off_nnz, long long* off_rptr,
+                             long long* off_x, long long* off_y) {
+  if (!p) return fail(GBS_EINVAL, "plan is NULL");
+  long long r = 0, z = 0, rp = 0, xo = 0, yo = 0;
+  for (int b = 0; b <= p->nmat; ++b) {
+    if (off_rows) off_rows[b] = r;
+    if (off_nnz) off_nnz[b] = z;
+    if (off_rptr) off_rptr[b] = rp;
+    if (off_x) off_x[b] = xo;
+    if (off_y) off_y[b] = yo;
+    if (b == p->nmat) break;
+    const gbs_batch_item& it = p->items[b];
+    r += it.m;
+    z += it.nnz;
+    rp += (long long)it.m + 1;
+    xo += (long long)it.n * p->k;
+    yo += (long long)it.m * p->k;
+  }
+  return GBS_OK;
+}
+
+int spmv_csr_batched_destroy(gbs_batch_plan* p) {
+  if (p) batch_free(p);
   return GBS_OK;
 }
 

@@ -62,6 +62,15 @@ cudaError_t gather_values(int dtype, const void* src, const int* perm, int nnz, 
 cudaError_t launch_sddmm(int dtype, int nnz, int k, const int* rows, const int* col_idx, const void* X, long long ldx,
                          const void* dY, long long lddy, void* dvals, cudaStream_t s);
 
+// Batched persistent kernel (batched.cu).  launch == false: set the shared-memory
+// attribute and report the resident CTAs per SM in *blocks_per_sm; launch == true: launch
+// `grid` CTAs of 256 threads over `descs` (device BatchDesc<T>[nmat]).
+cudaError_t batched_kernel_call(bool launch, int dtype, bool split, int G, bool vec16, const void* descs, int nmat,
+                                int total_items, int grid, size_t smem, int* blocks_per_sm, cudaStream_t s);
+
+// Message returned by gbs_last_error() on the calling thread (api.cu).
+void set_last_error(const char* msg);
+
 // Shared-memory bytes of one CTA (host helpers).
 size_t rows_smem(int dtype, int rows_per_cta, int tile);
 size_t merge_smem(int dtype, int g, bool vec16, int threads, int items);

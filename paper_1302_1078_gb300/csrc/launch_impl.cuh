@@ -127,8 +127,8 @@ size_t merge_smem_t(int g, bool vec16, int threads, int items) {
   size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
   size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
   size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
-  size_t d = ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;
-  size_t e = (size_t)threads * vec * sizeof(T);
+  size_t d = 2 * 32 * sizeof(int);
+  size_t e = 2 * (size_t)threads * vec * sizeof(T);
   return a + b + c + d + e;
 }
 

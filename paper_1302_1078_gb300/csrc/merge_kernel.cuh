@@ -13,9 +13,13 @@
 //     between them, so each nonzero costs one fused multiply-add per output
 //     element and row ends cost no FP64 work (GB300's FP64 pipe is the
 //     scarce resource; a masked FP64 instruction costs as much as a full one).
-//   * A row split across threads is finished by the thread where it ends,
-//     which adds the carries of the threads before it in a fixed order (a
-//     short look-back through shared memory) instead of a log-depth scan.
+//   * A row split across threads is finished by the thread where it ends.
+//     The carries of the threads before it arrive through a segmented
+//     inclusive scan keyed by row (Hillis-Steele over the merge threads of a
+//     warp, then a carry-in chain over the CTA's warps).  A scan step whose
+//     additions no lane needs is skipped for the whole warp, so a tile of
+//     short rows pays about one FP64 add per merge thread, and a hub row
+//     spanning many threads pays a logarithmic number, not a walk.
 //   * A row split across CTAs is finished by a separate fix-up pass over the
 //     per-CTA carries, in CTA order.  No atomics: the result is bitwise
 //     reproducible.
@@ -68,16 +72,18 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
   size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;           // s_rp
   size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;             // s_val
   size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;           // s_col
-  size_t d = ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;          // s_crow
-  size_t e = (size_t)nt * G * VEC * sizeof(T);                       // s_cval
+  size_t d = 2 * 32 * sizeof(int);                                   // s_wkey, s_cinkey
+  size_t e = 2 * (size_t)threads * VEC * sizeof(T);                  // s_wval, s_cinval (per warp: 32 lanes x VEC)
   return a + b + c + d + e;
 }
 
+// One merge-path tile b of the product (the whole CTA works on it).  Used by the
+// standalone kernel below and by the batched persistent kernel.
 template <typename T, int VEC, int G>
-__global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
+__device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.x;
   const int nt = blockDim.x / G;
+  const int nw = blockDim.x / 32;
   const int ipc = nt * a.items;
   const int2 cs = a.coords[b], ce = a.coords[b + 1];
   const int row0 = cs.x, nz0 = cs.y, row1 = ce.x, nz1 = ce.y;
@@ -90,9 +96,11 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
   off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
   int* s_col = reinterpret_cast<int*>(smem_raw + off);
   off += (((size_t)ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
-  int* s_crow = reinterpret_cast<int*>(smem_raw + off);
-  off += ((size_t)nt * sizeof(int) + 15) & ~(size_t)15;
-  T* s_cval = reinterpret_cast<T*>(smem_raw + off);
+  int* s_wkey = reinterpret_cast<int*>(smem_raw + off);
+  int* s_cinkey = s_wkey + 32;
+  off += 2 * 32 * sizeof(int);
+  T* s_wval = reinterpret_cast<T*>(smem_raw + off);      // [nw][32 * VEC]
+  T* s_cinval = s_wval + (size_t)blockDim.x * VEC;       // [nw][32 * VEC]
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
@@ -108,8 +116,12 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
   }
   __syncthreads();
 
-  const int t = threadIdx.x / G;
-  const int lane = threadIdx.x % G;
+  const int t = threadIdx.x / G;            // merge thread
+  const int lane = threadIdx.x % G;         // column lane inside the merge thread
+  const int wl = threadIdx.x & 31;          // lane in warp
+  const int w = threadIdx.x >> 5;           // warp
+  constexpr int MT = 32 / G;                // merge threads per warp
+  const int mt = wl / G;                    // merge thread inside the warp
   const int c_lo = lane * VEC;
   const bool col_active = c_lo < a.k;
   const bool col_full = c_lo + VEC <= a.k;
@@ -132,30 +144,33 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
   const int row_s = row0 + ri_s, nz_s = nz0 + ds - ri_s;
   const int row_e = row0 + ri_e, nz_e = nz0 + de - ri_e;
 
-  // the thread's first row started before its first nonzero: another thread holds its head
+  // the thread's first row started before its first nonzero: earlier threads hold its start
   const bool head_partial = (row_s < a.m) && (nz_s > s_rp[ri_s]);
 
   Acc<T> acc[VEC];
-  Acc<T> head[VEC];
+  T head[VEC];
   int head_row = -1;
   bool first = true;
   int row = row_s;
   const T* __restrict__ Xc = a.X + c_lo;
 
+  auto store_row = [&](int r, const T* out) {
+    T* yr = a.Y + (long long)r * a.ldy + c_lo;
+    if (col_full)
+      st_stream_vec<T, VEC>(yr, out);
+    else
+      for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+  };
   auto emit = [&](int r) {
+    T out[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
     if (first && head_partial) {
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) head[j] = acc[j];
+      for (int j = 0; j < VEC; ++j) head[j] = out[j];
       head_row = r;
     } else if (col_active) {
-      T* yr = a.Y + (long long)r * a.ldy + c_lo;
-      T out[VEC];
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
-      if (col_full)
-        st_stream_vec<T, VEC>(yr, out);
-      else
-        for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+      store_row(r, out);
     }
     first = false;
 #pragma unroll
@@ -199,59 +214,120 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
     ++row;
   }
 
-  // carry: the row still open at the end of this thread's share
-  if (lane == 0) s_crow[t] = row_e;
+  // ---- carries: segmented inclusive scan over merge threads, keyed by the open row
+  const int key = row_e;
+  T S[VEC];
 #pragma unroll
-  for (int j = 0; j < VEC; ++j) s_cval[((size_t)t * G + lane) * VEC + j] = acc[j].value();
+  for (int j = 0; j < VEC; ++j) S[j] = acc[j].value();
+#pragma unroll
+  for (int dd = 1; dd < MT; dd <<= 1) {
+    const int okey = __shfl_up_sync(0xffffffffu, key, dd * G);
+    T o[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) o[j] = __shfl_up_sync(0xffffffffu, S[j], dd * G);
+    const bool take = mt >= dd && okey == key;
+    if (__any_sync(0xffffffffu, take)) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j)
+        if (take) S[j] += o[j];
+    }
+  }
+  // warp summaries: key and run sum of each warp's last merge thread
+  if (mt == MT - 1) {
+    if (lane == 0) s_wkey[w] = key;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) s_wval[((size_t)w * 32 + lane) * VEC + j] = S[j];
+  }
   __syncthreads();
-
-  if (head_row >= 0 && col_active) {
-    // finish the split head row: own part, then the carries of earlier threads in order
+  // carry into warp ww: the run of the previous warp's last key, chained over whole-warp runs
+  if (threadIdx.x < G) {
+    const int c = threadIdx.x;
+    T cin[VEC];
+    int cin_key = -1;
+    for (int ww = 1; ww < nw; ++ww) {
+      const int k_prev = s_wkey[ww - 1];
+      T nv[VEC];
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      for (int tp = t - 1; tp >= 0 && s_crow[tp] == head_row; --tp) head[j].add_partial(s_cval[((size_t)tp * G + lane) * VEC + j]);
-    }
-    T* yr = a.Y + (long long)head_row * a.ldy + c_lo;
-    T out[VEC];
+      for (int j = 0; j < VEC; ++j) nv[j] = s_wval[((size_t)(ww - 1) * 32 + c) * VEC + j];
+      if (ww >= 2 && cin_key == k_prev) {
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) out[j] = head[j].value();
-    if (col_full)
-      st_stream_vec<T, VEC>(yr, out);
-    else
-      for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
-  }
-
-  if (t == nt - 1) {
-    // CTA carry: sum of the trailing thread carries of the row still open at the tile's end
-    const int crow = s_crow[nt - 1];
-    if (lane == 0) a.carry_row[b] = crow < a.m ? crow : -1;
-    if (col_active) {
-      for (int j = 0; j < VEC && c_lo + j < a.k; ++j) {
-        Acc<T> s;
-        for (int tp = nt - 1; tp >= 0 && s_crow[tp] == crow; --tp) s.add_partial(s_cval[((size_t)tp * G + lane) * VEC + j]);
-        a.carry_val[(size_t)b * a.k + c_lo + j] = s.value();
+        for (int j = 0; j < VEC; ++j) nv[j] += cin[j];
       }
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        cin[j] = nv[j];
+        s_cinval[((size_t)ww * 32 + c) * VEC + j] = nv[j];
+      }
+      cin_key = k_prev;
+      if (c == 0) s_cinkey[ww] = k_prev;
+    }
+    if (c == 0) s_cinkey[0] = -1;
+  }
+  __syncthreads();
+  const int wkey = s_cinkey[w];
+  {
+    const bool take = w > 0 && key == wkey;
+    if (__any_sync(0xffffffffu, take)) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j)
+        if (take) S[j] += s_cinval[((size_t)w * 32 + lane) * VEC + j];
     }
   }
+  // finish the split head row with the run that ends just before this merge thread
+  {
+    int pkey = __shfl_up_sync(0xffffffffu, key, G);
+    T ps[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) ps[j] = __shfl_up_sync(0xffffffffu, S[j], G);
+    if (mt == 0) {
+      pkey = w > 0 ? wkey : -1;
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) ps[j] = w > 0 ? s_cinval[((size_t)w * 32 + lane) * VEC + j] : T(0);
+    }
+    const bool take = head_row >= 0 && pkey == head_row;
+    if (__any_sync(0xffffffffu, take)) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j)
+        if (take) head[j] += ps[j];
+    }
+    if (head_row >= 0 && col_active) store_row(head_row, head);
+  }
+  if (t == nt - 1) {
+    // CTA carry: run sum of the row still open at the tile's end
+    if (lane == 0) a.carry_row[b] = key < a.m ? key : -1;
+    if (col_active)
+      for (int j = 0; j < VEC && c_lo + j < a.k; ++j) a.carry_val[(size_t)b * a.k + c_lo + j] = S[j];
+  }
+}
+
+template <typename T, int VEC, int G>
+__global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
+  merge_tile<T, VEC, G>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of
 // equal carry rows sums the run in CTA order and adds it to Y (row finished by a
 // later CTA, which has already written its own part).
 template <typename T>
+__device__ __forceinline__ void merge_fixup_one(int b, int ctas, int k, const int* __restrict__ carry_row,
+                                                const T* __restrict__ carry_val, T* __restrict__ Y, long long ldy) {
+  const int r = __ldcg(carry_row + b);
+  if (r < 0) return;
+  if (b > 0 && __ldcg(carry_row + b - 1) == r) return;
+  for (int c = 0; c < k; ++c) {
+    Acc<T> s;
+    for (int bb = b; bb < ctas && __ldcg(carry_row + bb) == r; ++bb) s.add_partial(__ldcg(carry_val + (size_t)bb * k + c));
+    T* yp = Y + (long long)r * ldy + c;
+    *yp = __ldcg(yp) + s.value();
+  }
+}
+
+template <typename T>
 __global__ void merge_fixup_kernel(int ctas, int k, const int* __restrict__ carry_row, const T* __restrict__ carry_val,
                                    T* __restrict__ Y, long long ldy) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ctas) return;
-  const int r = carry_row[b];
-  if (r < 0) return;
-  if (b > 0 && carry_row[b - 1] == r) return;
-  for (int c = 0; c < k; ++c) {
-    Acc<T> s;
-    for (int bb = b; bb < ctas && carry_row[bb] == r; ++bb) s.add_partial(carry_val[(size_t)bb * k + c]);
-    T* yp = Y + (long long)r * ldy + c;
-    *yp = *yp + s.value();
-  }
+  merge_fixup_one<T>(b, ctas, k, carry_row, carry_val, Y, ldy);
 }
 
 }  // namespace gbs

@@ -1,0 +1,127 @@
+"""Batched persistent launch (CUDA graph) against the per-matrix loop (bitwise) and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+NP = {torch.float64: np.float64, torch.float32: np.float32}
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    import paper_1302_1078_gb300 as g
+
+    g.lib()
+    return g
+
+
+def make_batch(specs, k, dtype, seed=0):
+    mats, Xs, Ys, host = [], [], [], []
+    for i, sp in enumerate(specs):
+        A = synth.batch_matrix(sp)
+        rp = torch.from_numpy(A.row_ptr).cuda()
+        ci = torch.from_numpy(A.col_idx).cuda()
+        v = torch.from_numpy(A.vals.astype(NP[dtype])).cuda()
+        Xh = synth.uniform(A.n * k, seed=seed + 17, stream=i).astype(NP[dtype])
+        X = torch.from_numpy(Xh).cuda() if k == 1 else torch.from_numpy(Xh.reshape(A.n, k)).cuda()
+        Y = torch.full((A.m,) if k == 1 else (A.m, k), float("nan"), dtype=dtype, device="cuda")
+        mats.append((rp, ci, v, A.n))
+        Xs.append(X)
+        Ys.append(Y)
+        host.append((A, Xh.reshape(A.n, k)))
+    return mats, Xs, Ys, host
+
+
+def check_vs_oracle(host, Ys, dtype, idx=None):
+    for b in (range(len(host)) if idx is None else idx):
+        A, Xh = host[b]
+        Yr, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), Xh)
+        got = Ys[b].double().cpu().numpy().reshape(Yr.shape)
+        assert np.all(np.abs(got - Yr) <= TOL[dtype] * R), f"matrix {b} ({A.name})"
+        assert np.all(got[R == 0] == 0)
+
+
+SMALL = synth.batch_specs(30, rows_lo=200, rows_hi=6000)
+
+
+@pytest.mark.parametrize("tune", [False, True], ids=["heuristic", "tuned"])
+@pytest.mark.parametrize("k,dtype", [(8, torch.float64), (1, torch.float64), (1, torch.float32), (4, torch.float32),
+                                     (3, torch.float64)], ids=["k8f64", "k1f64", "k1f32", "k4f32", "k3f64"])
+def test_batched_equals_looped_and_oracle(gbs, k, dtype, tune):
+    mats, Xs, Ys, host = make_batch(SMALL, k, dtype)
+    plan = gbs.BatchedPlan(mats, Xs, Ys, tune=tune, check=True)
+    info = plan.info()
+    ib = info["item_begin"]
+    assert ib[0] == 0 and all(b >= a for a, b in zip(ib, ib[1:])) and ib[-1] == info["total_items"]
+    variants = {c["variant"] for c in info["configs"]}
+    assert variants <= {1, 2}
+    plan.run()
+    torch.cuda.synchronize()
+    batched = [y.clone() for y in Ys]
+    check_vs_oracle(host, batched, dtype)
+    for y in Ys:
+        y.fill_(float("nan"))
+    plan.run_looped()
+    torch.cuda.synchronize()
+    for b in range(len(Ys)):
+        assert torch.equal(Ys[b], batched[b]), f"batched != looped for matrix {b}"
+    # graph replays are repeatable (merge completion counters reset themselves)
+    for _ in range(3):
+        plan.run()
+    torch.cuda.synchronize()
+    for b in range(len(Ys)):
+        assert torch.equal(Ys[b], batched[b]), f"replay differs for matrix {b}"
+
+
+def test_batched_forced_merge_and_new_operands(gbs):
+    """The R-MAT members take the merge path (completion counters, in-kernel fix-up); then new X/Y."""
+    import paper_1302_1078_gb300 as g
+
+    mats, Xs, Ys, host = make_batch(SMALL[:12], 8, torch.float64, seed=5)
+    plan = g.BatchedPlan(mats, Xs, Ys)
+    plan.run()
+    torch.cuda.synchronize()
+    check_vs_oracle(host, Ys, torch.float64)
+    # new operands
+    X2 = [torch.rand_like(x) for x in Xs]
+    Y2 = [torch.full_like(y, float("nan")) for y in Ys]
+    plan.run(X2, Y2)
+    torch.cuda.synchronize()
+    host2 = [(A, X2[b].cpu().numpy()) for b, (A, _) in enumerate(host)]
+    check_vs_oracle(host2, Y2, torch.float64)
+
+
+def test_batch_offsets_match_oracle(gbs):
+    mats, Xs, Ys, host = make_batch(SMALL[:20], 8, torch.float64)
+    plan = gbs.BatchedPlan(mats, Xs, Ys)
+    got = plan.offsets()
+    ms = np.array([A.m for A, _ in host], np.int32)
+    ns = np.array([A.n for A, _ in host], np.int32)
+    nz = np.array([A.nnz for A, _ in host], np.int64)
+    ref = oracle.batch_offsets(ms, ns, nz, 8)
+    for g_, r_ in zip(got, ref):
+        assert np.array_equal(g_, r_)
+
+
+def test_full_batch_512_k8(gbs):
+    """The batched configuration at full size: 512 matrices, rows log-uniform in 1k-200k,
+    k = 8, FP64, tuned; batched equals looped bitwise, a sample of matrices checked against
+    the oracle."""
+    specs = synth.batch_specs(512)
+    mats, Xs, Ys, host = make_batch(specs, 8, torch.float64, seed=3)
+    plan = gbs.BatchedPlan(mats, Xs, Ys, tune=True)
+    plan.run()
+    torch.cuda.synchronize()
+    batched = [y.clone() for y in Ys]
+    plan.run_looped()
+    torch.cuda.synchronize()
+    for b in range(len(Ys)):
+        assert torch.equal(Ys[b], batched[b]), f"batched != looped for matrix {b}"
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.choice(len(specs), 24, replace=False).tolist()) | {0, 1, 2, 511})
+    check_vs_oracle(host, batched, torch.float64, sample)
