@@ -146,6 +146,34 @@ int spmv_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, cons
 int spmv_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
                  int dtype, const void* x, void* y, const gbs_config* cfg, void* stream);
 
+/*
+ * y <- A x, as spmv_csr, for callers that must not allocate device memory:
+ * for example a host application that owns and accounts for every device
+ * allocation (a memory-capped service, a plug-in host), or a latency-critical
+ * loop where an allocation could block or fail under memory pressure.  The
+ * paper has no counterpart.
+ *
+ * The merge-path scratch (tile coordinates and per-tile carries) comes from a
+ * 4 MiB static array in the library's device memory, which every GPU that
+ * loads the library holds until the process exits; no cudaMalloc, cudaFree
+ * or other allocating routine is called.  Limit: the scratch of one call is
+ * about 20 bytes (FP64; 16 for FP32) per 3840 rows + nonzeros, so m + nnz up
+ * to about 8.05e8 (FP64) or 1.0e9 (FP32) fits; larger sizes return
+ * GBS_EUNSUPPORTED with a message (gbs_last_error) before anything is
+ * launched.  Same dtypes, arguments,
+ * results and determinism as spmv_csr; GBSPMV_CHECKED validation is not run.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it: make that first call before any
+ * stream capture.  Every call shares the one array, whose contents persist
+ * from the previous call; each call writes every scratch element before
+ * reading it, so nothing needs clearing.  Calls that overlap on the GPU (on
+ * different streams, or from different threads without ordering) race on
+ * the array and may produce wrong results: order them on one stream.
+ */
+int spmv_csr_noalloc(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+                     int dtype, const void* x, void* y, void* stream);
+
 /* ------------------------------------------------------------------ SpMM */
 /*
  * Y <- A X  (Sec. 5): X is n x k with leading dimension ldx >= k, Y is m x k

@@ -65,6 +65,7 @@ SIGNATURES = {
     "gbs_default_config": (I32, [ctypes.POINTER(gbs_stats), I32, I32, ctypes.POINTER(gbs_config)]),
     "spmv_csr": (I32, [I32, I32, I32, P, P, P, I32, P, P, P]),
     "spmv_csr_cfg": (I32, [I32, I32, I32, P, P, P, I32, P, P, ctypes.POINTER(gbs_config), P]),
+    "spmv_csr_noalloc": (I32, [I32, I32, I32, P, P, P, I32, P, P, P]),
     "spmm_csr": (I32, [I32, I32, I32, P, P, P, I32, I32, P, I32, P, I32, P]),
     "spmm_csr_cfg": (I32, [I32, I32, I32, P, P, P, I32, I32, P, I32, P, I32, ctypes.POINTER(gbs_config), P]),
     "gbs_plan_create": (I32, [ctypes.POINTER(P), I32, I32, I32, P, P, I32, I32, I32, P]),
