@@ -66,7 +66,10 @@ typedef enum { GBS_F64 = 0, GBS_F32 = 1 } gbs_dtype;
 typedef enum {
   GBS_VARIANT_AUTO = 0,   /* let the library choose from the row-length statistics */
   GBS_VARIANT_ROWS = 1,   /* sub-warp per row: `lanes` lanes share one row */
-  GBS_VARIANT_MERGE = 2   /* merge-path: equal shares of (rows + nonzeros) per thread */
+  GBS_VARIANT_MERGE = 2,  /* merge-path: equal shares of (rows + nonzeros) per thread */
+  GBS_VARIANT_ROWS_TMA = 3 /* ROWS with persistent CTAs and a double-buffered bulk-copy (TMA)
+                              pipeline; plans only (the plan sizes the tile to the largest
+                              row block); needs 16-byte aligned vals and col_idx, else runs as ROWS */
 } gbs_variant;
 
 /*
@@ -213,6 +216,12 @@ int gbs_plan_set_config(gbs_plan* plan, const gbs_config* cfg);
 int gbs_plan_get_stats(const gbs_plan* plan, gbs_stats* out);
 /* y <- A x (plan k must be 1) or Y <- A X (ldx, ldy >= plan k). */
 int spmv_csr_plan(const gbs_plan* plan, const void* vals, const void* x, void* y, void* stream);
+/*
+ * Device status of the plan's bounded waits (host `*status`; bit 0: a pipeline
+ * wait of GBS_VARIANT_ROWS_TMA timed out and its CTA returned early, so the
+ * result of that call is incomplete).  Reads and clears it; synchronises `stream`.
+ */
+int gbs_plan_status(gbs_plan* plan, int* status, void* stream);
 int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx, void* Y, int ldy,
                   void* stream);
 

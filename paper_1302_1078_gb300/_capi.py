@@ -33,6 +33,7 @@ GBS_F32 = 1
 VARIANT_AUTO = 0
 VARIANT_ROWS = 1
 VARIANT_MERGE = 2
+VARIANT_ROWS_TMA = 3
 
 PLAN_TUNE = 1
 PLAN_CHECK = 2
@@ -74,6 +75,7 @@ SIGNATURES = {
     "gbs_plan_set_config": (I32, [P, ctypes.POINTER(gbs_config)]),
     "gbs_plan_get_stats": (I32, [P, ctypes.POINTER(gbs_stats)]),
     "spmv_csr_plan": (I32, [P, P, P, P, P]),
+    "gbs_plan_status": (I32, [P, ctypes.POINTER(I32), P]),
     "spmm_csr_plan": (I32, [P, P, P, I32, P, I32, P]),
     "gbs_transpose_plan": (I32, [ctypes.POINTER(P), I32, I32, I32, P, P, P]),
     "gbs_tplan_arrays": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),

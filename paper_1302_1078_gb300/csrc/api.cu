@@ -16,6 +16,7 @@
 #include "launch.h"
 #include "merge_kernel.cuh"
 #include "rows_kernel.cuh"
+#include "rows_tma.cuh"
 
 using namespace gbs;
 
@@ -82,7 +83,7 @@ int default_items(int g, int threads) {
 gbs_config normalize(const gbs_config& c, int dtype) {
   gbs_config r = c;
   if (r.threads <= 0) r.threads = 256;
-  if (r.variant == GBS_VARIANT_ROWS) {
+  if (r.variant == GBS_VARIANT_ROWS || r.variant == GBS_VARIANT_ROWS_TMA) {
     if (r.lanes <= 0) r.lanes = 1;
     if (r.tile_nnz <= 0) r.tile_nnz = dtype == GBS_F64 ? 2048 : 3072;
   }
@@ -95,12 +96,13 @@ struct MergeGeom {
 };
 
 int check_cfg(const gbs_config& c) {
-  if (c.variant != GBS_VARIANT_ROWS && c.variant != GBS_VARIANT_MERGE)
-    return fail(GBS_EINVAL, "variant must be ROWS or MERGE after resolution");
+  if (c.variant != GBS_VARIANT_ROWS && c.variant != GBS_VARIANT_MERGE && c.variant != GBS_VARIANT_ROWS_TMA)
+    return fail(GBS_EINVAL, "variant must be ROWS, MERGE or ROWS_TMA after resolution");
+  if (c.variant == GBS_VARIANT_ROWS_TMA && c.threads > 256) return fail(GBS_EINVAL, "ROWS_TMA threads must be <= 256");
   if (c.threads % 32 != 0 || c.threads < 32 || c.threads > 1024) return fail(GBS_EINVAL, "threads must be 32..1024, multiple of 32");
   if (c.variant == GBS_VARIANT_MERGE && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
   if (c.lanes != 0 && !pow2_lanes(c.lanes)) return fail(GBS_EINVAL, "lanes must be 1, 2, 4, 8, 16 or 32");
-  if (c.variant == GBS_VARIANT_ROWS && (c.tile_nnz < 32 || c.tile_nnz > (1 << 14)))
+  if ((c.variant == GBS_VARIANT_ROWS || c.variant == GBS_VARIANT_ROWS_TMA) && (c.tile_nnz < 32 || c.tile_nnz > (1 << 14)))
     return fail(GBS_EINVAL, "tile_nnz must be in [32, 16384]");
   if (c.variant == GBS_VARIANT_MERGE && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
   return GBS_OK;
@@ -153,13 +155,25 @@ MergeGeom merge_geom(const gbs_config& cfg, int m, int nnz, int dtype, int k, bo
 // configuration.  Merge scratch comes from `mb` if given (plan), else from the stream-ordered
 // allocator.  `coords_ready`: the partition in mb is valid for this configuration.
 int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx, void* Y, long long ldy,
-                const gbs_config& cfg, MergeBuffers* mb, bool coords_ready, cudaStream_t s) {
+                const gbs_config& cfg, MergeBuffers* mb, bool coords_ready, cudaStream_t s, int* status = nullptr) {
   if (A.m == 0 || k == 0) return GBS_OK;
   const bool vec16 = dense_vec16(dtype, k, X, ldx, Y, ldy);
   const int P = panel_cols(dtype, vec16);
   const size_t es = dsize(dtype);
   cudaError_t e = cudaSuccess;
-  if (cfg.variant == GBS_VARIANT_ROWS) {
+  if (cfg.variant == GBS_VARIANT_ROWS_TMA && status && aligned16(A.vals) && aligned16(A.col_idx)) {
+    for (int c0 = 0; c0 < k; c0 += P) {
+      const int kp = std::min(P, k - c0);
+      int lanes = cfg.lanes;
+      if (k > 1) lanes = std::max(lanes, col_lanes(kp, dtype, vec16));
+      DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
+      e = dtype == GBS_F64 ? launch_rows_tma_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, status, s)
+                           : launch_rows_tma_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ROWS_TMA launch");
+    }
+    return GBS_OK;
+  }
+  if (cfg.variant == GBS_VARIANT_ROWS || cfg.variant == GBS_VARIANT_ROWS_TMA) {
     for (int c0 = 0; c0 < k; c0 += P) {
       const int kp = std::min(P, k - c0);
       int lanes = cfg.lanes;
@@ -290,6 +304,33 @@ int compute_stats(int m, int n, int nnz, const int* rp, gbs_stats* out, cudaStre
   return GBS_OK;
 }
 
+__global__ void block_max_nnz_kernel(const int* __restrict__ rp, int m, int rpc, int* __restrict__ out) {
+  const int nb = (m + rpc - 1) / rpc;
+  int mx = 0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+    mx = max(mx, rp[min(m, (b + 1) * rpc)] - rp[b * rpc]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+// Largest nonzero count of a block of rpc consecutive rows (synchronises s).
+int block_max_nnz(const int* rp, int m, int rpc, int* out, cudaStream_t s) {
+  int* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (block max)");
+  e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    const int nb = (m + rpc - 1) / rpc;
+    block_max_nnz_kernel<<<std::min(1024, (nb + 255) / 256), 256, 0, s>>>(rp, m, rpc, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "block max nnz");
+}
+
 gbs_config heuristic_config(const gbs_stats& st, int dtype, int k) {
   gbs_config c{};
   c.threads = 256;
@@ -339,6 +380,9 @@ __global__ void fp64_probe_kernel(double* __restrict__ out, int iters) {
 namespace gbs {
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
+size_t rows_tma_smem(int dtype, int rpc, int tile) {
+  return dtype == GBS_F64 ? rows_tma_smem_bytes<double>(rpc, tile) : rows_tma_smem_bytes<float>(rpc, tile);
+}
 
 // Start coordinates of every merge-path tile: one thread per tile boundary.
 __global__ void merge_partition_kernel(const int* __restrict__ row_ptr, int m, int nnz, int ctas,
@@ -504,6 +548,7 @@ struct gbs_plan {
   gbs_config cfg{};
   MergeBuffers mb{};
   bool coords_ready = false;
+  int* status = nullptr;  // device word: bounded-wait status of the pipelined variant
 };
 
 namespace {
@@ -516,6 +561,20 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
     p->mb = MergeBuffers{};
   }
   p->coords_ready = false;
+  if (p->cfg.variant == GBS_VARIANT_ROWS_TMA && p->m > 0) {
+    // the tile must hold the largest row block: measure it on the device
+    int lanes = p->cfg.lanes;
+    if (p->k > 1) lanes = std::max(lanes, col_lanes(std::min(panel_cols(p->dtype, true), p->k), p->dtype, true));
+    const int rpc = p->cfg.threads / lanes;
+    int mx = 0;
+    int rc = block_max_nnz(p->row_ptr, p->m, rpc, &mx, s);
+    if (rc) return rc;
+    const int tile = ((mx + 8 + 31) / 32) * 32;
+    const size_t smem = rows_tma_smem(p->dtype, rpc, tile);
+    if (tile > (1 << 14) || smem > 227 * 1024) return fail(GBS_EUNSUPPORTED, "row blocks too large for ROWS_TMA");
+    p->cfg.tile_nnz = tile;
+    return GBS_OK;
+  }
   if (p->cfg.variant != GBS_VARIANT_MERGE || p->m == 0) return GBS_OK;
   // the partition depends on the lanes per merge thread, which depend on whether a call
   // can use 128-bit column access; the plan is made for that case (k > 1) and calls that
@@ -546,7 +605,7 @@ int plan_run(const gbs_plan* p, const void* vals, const void* X, long long ldx, 
     MergeBuffers mb = p->mb;
     return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, &mb, p->coords_ready, s);
   }
-  return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s);
+  return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s, p->status);
 }
 
 // Candidate configurations for the tuner.
@@ -577,11 +636,16 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     }
     add(GBS_VARIANT_ROWS, 1, 128, fit_tile(128, 1), 0);
     add(GBS_VARIANT_ROWS, 2, 128, fit_tile(128, 2), 0);
+    for (int l : {1, 2, 4})
+      for (int th : {128, 256})
+        if (l == 1 || p->stats.mean_row >= 0.5 * l) add(GBS_VARIANT_ROWS_TMA, l, th, 0, 0);
     for (int it : {7, 11, 15, 23, 31}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 256, base_tile / 2, 0);
+    add(GBS_VARIANT_ROWS_TMA, 0, 128, 0, 0);
+    add(GBS_VARIANT_ROWS_TMA, 0, 256, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 256, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
   }
@@ -670,6 +734,12 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   p->row_ptr = row_ptr;
   p->col_idx = col_idx;
   cudaGetDevice(&p->device);
+  if (cudaMalloc(reinterpret_cast<void**>(&p->status), 256) != cudaSuccess ||
+      cudaMemsetAsync(p->status, 0, 256, s) != cudaSuccess) {
+    if (p->status) cudaFree(p->status);
+    delete p;
+    return fail(GBS_ENOMEM, "plan status word");
+  }
   rc = compute_stats(m, n, nnz, row_ptr, &p->stats, s);
   if (rc == GBS_OK) {
     p->cfg = heuristic_config(p->stats, dtype, k);
@@ -677,6 +747,7 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   }
   if (rc != GBS_OK) {
     if (p->mb.base) cudaFree(p->mb.base);
+    cudaFree(p->status);
     delete p;
     return rc;
   }
@@ -687,8 +758,18 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
 int gbs_plan_destroy(gbs_plan* plan) {
   if (!plan) return GBS_OK;
   if (plan->mb.base) cudaFree(plan->mb.base);
+  if (plan->status) cudaFree(plan->status);
   delete plan;
   return GBS_OK;
+}
+
+int gbs_plan_status(gbs_plan* plan, int* status, void* stream) {
+  if (!plan || !status) return fail(GBS_EINVAL, "NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(status, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "plan status");
 }
 
 int gbs_plan_get_config(const gbs_plan* plan, gbs_config* cfg) {

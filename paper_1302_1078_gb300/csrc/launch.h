@@ -36,6 +36,14 @@ cudaError_t launch_rows_f64(const CsrView& A, const DenseView& D, int lanes, boo
 cudaError_t launch_rows_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
                             int row_base, int rows, cudaStream_t s);
 
+// ROWS_TMA variant (persistent, bulk-copy pipeline).  tile must hold the largest block's
+// nonzeros + 8; vals and col_idx 16-byte aligned; status: device int (bit 0 = wait timeout).
+cudaError_t launch_rows_tma_f64(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                                int* status, cudaStream_t s);
+cudaError_t launch_rows_tma_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                                int* status, cudaStream_t s);
+size_t rows_tma_smem(int dtype, int rows_per_cta, int tile);
+
 // MERGE variant: partition (coords) must have been computed for (threads / g) * items
 // items per CTA.  g lanes per merge thread (columns), g * VEC >= k.
 cudaError_t launch_merge_f64(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,

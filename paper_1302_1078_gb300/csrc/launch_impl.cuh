@@ -1,9 +1,12 @@
 // Template launchers behind launch.h, instantiated once per dtype in
 // kernels_f64.cu / kernels_f32.cu so that the two compile in parallel.
 #pragma once
+#include <algorithm>
+
 #include "launch.h"
 #include "merge_kernel.cuh"
 #include "rows_kernel.cuh"
+#include "rows_tma.cuh"
 
 namespace gbs {
 
@@ -60,6 +63,64 @@ cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool 
     case 8: return rows_lanes<T, 8>(a, split, vec16, grid, threads, smem, s);
     case 16: return rows_lanes<T, 16>(a, split, vec16, grid, threads, smem, s);
     case 32: return rows_lanes<T, 32>(a, split, vec16, grid, threads, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int VEC, int LANES, bool SPLIT>
+static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* status, int threads, size_t smem,
+                               cudaStream_t s) {
+  auto kern = rows_tma_kernel<T, VEC, LANES, SPLIT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int bps = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem)) != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (bps < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(nblocks, bps * sms);
+  kern<<<grid, threads, smem, s>>>(a, nblocks, nnz, status);
+  return cudaGetLastError();
+}
+
+template <typename T, int LANES>
+static cudaError_t rows_tma_lanes(const RowsArgs<T>& a, bool split, bool vec16, int nblocks, int nnz, int* status,
+                                  int threads, size_t smem, cudaStream_t s) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if (split) return rows_tma_go<T, 1, LANES, true>(a, nblocks, nnz, status, threads, smem, s);
+  if (vec16) return rows_tma_go<T, V, LANES, false>(a, nblocks, nnz, status, threads, smem, s);
+  return rows_tma_go<T, 1, LANES, false>(a, nblocks, nnz, status, threads, smem, s);
+}
+
+template <typename T>
+cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
+                              int* status, cudaStream_t s) {
+  if (A.m <= 0) return cudaSuccess;
+  RowsArgs<T> a;
+  a.m = A.m;
+  a.k = D.k;
+  a.row_ptr = A.row_ptr;
+  a.col_idx = A.col_idx;
+  a.vals = static_cast<const T*>(A.vals);
+  a.X = static_cast<const T*>(D.X);
+  a.Y = static_cast<T*>(D.Y);
+  a.ldx = D.ldx;
+  a.ldy = D.ldy;
+  a.tile = tile;
+  a.row_base = 0;
+  a.aligned_vals = true;
+  a.aligned_cols = true;
+  const int rpc = threads / lanes;
+  const int nblocks = (A.m + rpc - 1) / rpc;
+  const size_t smem = rows_tma_smem_bytes<T>(rpc, tile);
+  const bool split = D.k == 1;
+  switch (lanes) {
+    case 1: return rows_tma_lanes<T, 1>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 2: return rows_tma_lanes<T, 2>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 4: return rows_tma_lanes<T, 4>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 8: return rows_tma_lanes<T, 8>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 16: return rows_tma_lanes<T, 16>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 32: return rows_tma_lanes<T, 32>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,258 @@
+// ROWS variant with persistent CTAs and a double-buffered bulk-copy pipeline
+// ("ROWS_TMA").
+//
+// Same per-row arithmetic as rows_kernel.cuh (the paper's row-wise kernel,
+// Sec. 4.1 / Sec. 5, with LANES lanes per row), but the nonzero stream of
+// the next row block is copied into shared memory by the bulk-copy (TMA)
+// engine while the CTA computes the current block:
+//   * one thread issues cp.async.bulk copies of the block's vals and col_idx
+//     ranges and arms an mbarrier with the expected byte count;
+//   * every thread waits on that mbarrier (bounded) before computing;
+//   * row_ptr of the block after next is prefetched into registers during
+//     the compute and parked in a third row-pointer slot.
+// CTAs are persistent (grid = resident CTA slots); CTA c takes row blocks
+// c, c + grid, c + 2 grid, ...  The tile must hold the largest row block's
+// nonzeros (+ 8); the plan checks this.  vals and col_idx must be 16-byte
+// aligned.  The copies round the range out to 4-element boundaries; the
+// last <= 3 nonzeros of the arrays, which cannot be rounded up without
+// reading past the end, are loaded with plain loads.
+//
+// Every wait is bounded: on timeout the kernel sets the device error flag,
+// waits (again bounded) for the copies it issued, and returns.
+#pragma once
+#include "device_common.cuh"
+#include "rows_kernel.cuh"
+
+namespace gbs {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename T>
+__host__ __device__ inline size_t rows_tma_smem_bytes(int rpc, int tile) {
+  size_t bars = 16;
+  size_t rp = 3 * (((size_t)(rpc + 1) * sizeof(int) + 15) & ~(size_t)15);
+  size_t val = (((size_t)tile + 8) * sizeof(T) + 15) & ~(size_t)15;
+  size_t col = (((size_t)tile + 8) * sizeof(int) + 15) & ~(size_t)15;
+  return bars + rp + 2 * (val + col);
+}
+
+template <typename T, int VEC, int LANES, bool SPLIT>
+__global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblocks, int nnz, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int rpc = blockDim.x / LANES;
+  const int tile = a.tile;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  const size_t rp_stride = ((size_t)(rpc + 1) * sizeof(int) + 15) & ~(size_t)15;
+  int* s_rp_base = reinterpret_cast<int*>(smem_raw + 16);
+  unsigned char* stage_base = smem_raw + 16 + 3 * rp_stride;
+  const size_t val_bytes = (((size_t)tile + 8) * sizeof(T) + 15) & ~(size_t)15;
+  const size_t col_bytes = (((size_t)tile + 8) * sizeof(int) + 15) & ~(size_t)15;
+  auto s_rp = [&](int slot) { return reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(s_rp_base) + slot * rp_stride); };
+  auto s_val = [&](int st) { return reinterpret_cast<T*>(stage_base + st * (val_bytes + col_bytes)); };
+  auto s_col = [&](int st) { return reinterpret_cast<int*>(stage_base + st * (val_bytes + col_bytes) + val_bytes); };
+
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  const int tid = threadIdx.x;
+
+  auto blk_of = [&](int i) { return blockIdx.x + i * gridDim.x; };
+  auto rows_of = [&](int blk) { return min(rpc, a.m - blk * rpc); };
+
+  // row_ptr entries of block blk into registers (thread t holds entry t; thread 0 also the last)
+  auto load_rp = [&](int blk, int& v0, int& v1) {
+    v0 = 0;
+    v1 = 0;
+    if (blk < nblocks) {
+      const int nr = rows_of(blk);
+      if (tid <= nr) v0 = ld_stream(a.row_ptr + blk * rpc + tid, pol_stream);
+      if (tid == 0 && nr >= (int)blockDim.x) v1 = ld_stream(a.row_ptr + blk * rpc + nr, pol_stream);
+    }
+  };
+  auto park_rp = [&](int blk, int slot, int v0, int v1) {
+    if (blk < nblocks) {
+      const int nr = rows_of(blk);
+      int* d = s_rp(slot);
+      if (tid <= nr) d[tid] = v0;
+      if (tid == 0 && nr >= (int)blockDim.x) d[nr] = v1;
+    }
+  };
+  // the copy of block blk into stage st (thread 0); rounds [s, e) out to 4-element boundaries
+  auto issue = [&](int blk, int slot, int st) {
+    const int nr = rows_of(blk);
+    const int s = s_rp(slot)[0], e = s_rp(slot)[nr];
+    const int a0 = s & ~3;
+    int e_cp = (e + 3) & ~3;
+    if (e_cp > nnz) e_cp = e & ~3;
+    const uint32_t nv = e_cp > a0 ? (uint32_t)(e_cp - a0) : 0u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bars[st], nv * (uint32_t)(sizeof(T) + sizeof(int)));
+    if (nv) {
+      bulk_copy_g2s(s_val(st), a.vals + a0, nv * (uint32_t)sizeof(T), &bars[st]);
+      bulk_copy_g2s(s_col(st), a.col_idx + a0, nv * (uint32_t)sizeof(int), &bars[st]);
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    int v0, v1;
+    load_rp(blk_of(0), v0, v1);
+    park_rp(blk_of(0), 0, v0, v1);
+    load_rp(blk_of(1), v0, v1);
+    park_rp(blk_of(1), 1, v0, v1);
+  }
+  __syncthreads();
+  if (tid == 0 && blk_of(0) < nblocks) issue(blk_of(0), 0, 0);
+
+  const int g = tid / LANES;
+  const int lane = tid % LANES;
+  const int c_lo = SPLIT ? 0 : lane * VEC;
+  const bool col_active = SPLIT ? true : (c_lo < a.k);
+  const bool col_full = SPLIT ? true : (c_lo + VEC <= a.k);
+  const T* __restrict__ Xc = a.X + c_lo;
+  __shared__ int s_abort;
+  if (tid == 0) s_abort = 0;
+  __syncthreads();
+
+  int i = 0;
+  for (; blk_of(i) < nblocks; ++i) {
+    const int blk = blk_of(i), st = i & 1, slot = i % 3;
+    const uint32_t parity = (uint32_t)((i >> 1) & 1);
+    if (tid == 0 && blk_of(i + 1) < nblocks) issue(blk_of(i + 1), (i + 1) % 3, st ^ 1);
+    int pv0, pv1;
+    load_rp(blk_of(i + 2), pv0, pv1);  // consumed at the end of this iteration
+    if (!mbar_wait_bounded(&bars[st], parity)) {
+      atomicOr(status, 1);
+      s_abort = 1;
+    }
+    const int nr = rows_of(blk);
+    const int* rp = s_rp(slot);
+    const int s = rp[0], e = rp[nr];
+    const int a0 = s & ~3;
+    int e_cp = (e + 3) & ~3;
+    if (e_cp > nnz) e_cp = e & ~3;
+    T* sv = s_val(st);
+    int* sc = s_col(st);
+    if (e_cp < e) {
+      // the arrays' last <= 3 nonzeros: plain loads (block-uniform branch)
+      if (tid < e - e_cp) {
+        sv[e_cp - a0 + tid] = a.vals[e_cp + tid];
+        sc[e_cp - a0 + tid] = a.col_idx[e_cp + tid];
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+
+    // ---- compute the rows of block blk from stage st
+    const bool active = g < nr;
+    Acc<T> acc[VEC];
+    if (active && col_active) {
+      const int rs = rp[g], re = rp[g + 1];
+      constexpr int STEP = SPLIT ? LANES : 1;
+      int p = rs + (SPLIT ? lane : 0);
+      if (col_full) {
+        for (; p + (kUnroll - 1) * STEP < re; p += kUnroll * STEP) {
+          T v[kUnroll];
+          int c[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            v[u] = sv[p + u * STEP - a0];
+            c[u] = sc[p + u * STEP - a0];
+          }
+          Vec<T, VEC> xv[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+        }
+        for (; p < re; p += STEP) {
+          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p - a0] * a.ldx, pol_keep);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) acc[j].add(sv[p - a0], xv.v[j]);
+        }
+      } else {
+        const int nv = a.k - c_lo;
+        for (; p < re; p += STEP) {
+          const T* xr = Xc + (long long)sc[p - a0] * a.ldx;
+#pragma unroll
+          for (int j = 0; j < VEC; ++j)
+            if (j < nv) acc[j].add(sv[p - a0], ld_keep(xr + j, pol_keep));
+        }
+      }
+    }
+    const int r0 = blk * rpc;
+    if constexpr (SPLIT) {
+      T sum = acc[0].value();
+#pragma unroll
+      for (int o = LANES / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, LANES);
+      if (active && lane == 0) st_stream(a.Y + (long long)(r0 + g) * a.ldy, sum);
+    } else {
+      if (active && col_active) {
+        T out[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
+        T* yr = a.Y + (long long)(r0 + g) * a.ldy + c_lo;
+        if (col_full)
+          st_stream_vec<T, VEC>(yr, out);
+        else
+          for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+      }
+    }
+    park_rp(blk_of(i + 2), (i + 2) % 3, pv0, pv1);
+    fence_proxy_async_smem();  // generic writes to the stage before the bulk engine reuses it
+    __syncthreads();           // stage st and row slot are free again
+  }
+  if (s_abort) {
+    // a wait gave up at iteration i: wait (bounded) for the copies this CTA issued, the
+    // current stage's and, if issued, the next stage's, before the CTA leaves
+    mbar_wait_bounded(&bars[i & 1], (uint32_t)((i >> 1) & 1));
+    if (blk_of(i + 1) < nblocks) mbar_wait_bounded(&bars[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1));
+  }
+}
+
+}  // namespace gbs

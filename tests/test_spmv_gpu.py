@@ -5,6 +5,8 @@ tol = 1e-12 for FP64 and 2e-5 for FP32 inputs; an entry whose bound is 0 must
 be exactly 0.  Index-valued facts (closed forms with integer results,
 permutations) must match bitwise.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -252,3 +254,68 @@ def test_full_size_spmv_tuned_plan(gbs, name):
     assert_close(y, y_ref, r, torch.float64, f"{name} {plan.config}")
     y2 = gbs.spmv_csr(rp, ci, v, torch.from_numpy(x).cuda())
     assert_close(y2, y_ref, r, torch.float64, f"{name} auto")
+
+
+# ------------------------------------------- pipelined ROWS (bulk-copy staging)
+
+TMA_SHAPES = [dict(lanes=1, threads=128), dict(lanes=1, threads=256), dict(lanes=2, threads=64),
+              dict(lanes=4, threads=256), dict(lanes=8, threads=128), dict(lanes=32, threads=256)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("name", ["stencil2d_64", "stencil3d_21", "banded_30k", "rmat_14", "random_rect",
+                                  "random_dup_unsorted", "empty_nnz", "one_row"])
+def test_rows_tma_variant(gbs, name, k, dtype):
+    from paper_1302_1078_gb300 import _capi
+
+    A = matrix(name)
+    rp, ci, v = dev_csr(A, dtype)
+    if k == 1:
+        x = synth.uniform(A.n, seed=3, stream=k).astype(NP[dtype])
+        Y_ref, R = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), x)
+        xd = torch.from_numpy(x).cuda()
+    else:
+        X = synth.uniform(A.n * k, seed=3, stream=k).reshape(A.n, k).astype(NP[dtype])
+        Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), X)
+        xd = torch.from_numpy(X).cuda()
+    plan = gbs.Plan(rp, ci, A.n, dtype, k)
+    for shape in TMA_SHAPES:
+        cfg = dict(variant=_capi.VARIANT_ROWS_TMA, **shape)
+        try:
+            plan.set_config(cfg)
+        except gbs.GbsError as e:
+            # a row block larger than the shared-memory tile: the plan refuses the variant
+            assert e.status == _capi.GBS_EUNSUPPORTED
+            continue
+        assert plan.config["variant"] == _capi.VARIANT_ROWS_TMA
+        out = torch.full(Y_ref.shape if k > 1 else (A.m,), float("nan"), dtype=dtype, device="cuda")
+        if k == 1:
+            plan.spmv(v, xd, out)
+        else:
+            plan.spmm(v, xd, out)
+        assert_close(out, Y_ref, R, dtype, f"{name} k={k} {shape}")
+        # misaligned values (8 bytes off a 16-byte boundary): the plan falls back to ROWS
+        buf = torch.empty(v.numel() + 4, dtype=dtype, device="cuda")
+        vm = buf[1:1 + v.numel()]
+        vm.copy_(v)
+        out2 = torch.full_like(out, float("nan"))
+        if k == 1:
+            plan.spmv(vm, xd, out2)
+        else:
+            plan.spmm(vm, xd, out2)
+        assert_close(out2, Y_ref, R, dtype, f"{name} k={k} {shape} misaligned")
+    st = ctypes.c_int(-1)
+    gbs.lib().gbs_plan_status(plan._h, ctypes.byref(st), torch.cuda.current_stream().cuda_stream)
+    assert st.value == 0
+
+
+def test_rows_tma_refuses_huge_blocks(gbs):
+    from paper_1302_1078_gb300 import _capi
+
+    A = matrix("hub")
+    rp, ci, v = dev_csr(A)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, 1)
+    with pytest.raises(gbs.GbsError) as e:
+        plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, lanes=1, threads=256))
+    assert e.value.status == _capi.GBS_EUNSUPPORTED
