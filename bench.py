@@ -74,6 +74,39 @@ WORKLOAD_TEXT = {
 }
 
 
+# Source files that define each variant's kernel: a DRAM-traffic figure recorded from an ncu
+# capture (profiles/traffic.txt) is reported only while these files are unchanged.
+KERNEL_SOURCES = {
+    1: ["rows_kernel.cuh", "device_common.cuh"],
+    2: ["merge_kernel.cuh", "device_common.cuh"],
+    3: ["rows_tma.cuh", "rows_kernel.cuh", "device_common.cuh", "df64.cuh"],
+}
+
+
+def kernel_source_hash(variant: int) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(variant, []):
+        with open(os.path.join(ROOT, "paper_1302_1078_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(variant: int, matrix: str):
+    """DRAM bytes per launch from profiles/traffic.txt (lines: variant hash bytes matrix command...),
+    or None when no capture matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash(variant)
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == str(variant) and f[1] == want and f[3] == matrix:
+            return float(f[2])
+    return None
+
+
 def compulsory_bytes(m, n, nnz, k, es=8):
     """Sec. 4.2 / Sec. 5 application-bandwidth model with (m+1) row pointers:
     es*nnz + 4*nnz + 4*(m+1) + es*n*k + es*m*k."""
@@ -270,7 +303,7 @@ def run_gpu(args, rank, world, local_rank):
             X = synth.uniform(A.n * k, seed=synth.BASE_SEED + 11 + rank, stream=k)
             Xd = torch.from_numpy(X).to(dev).reshape(A.n, k) if k > 1 else torch.from_numpy(X).to(dev)
             Yd = torch.empty((A.m, k) if k > 1 else (A.m,), dtype=torch.float64, device=dev)
-            plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True)
+            plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True, emulate=args.emulate)
             items.append(dict(name=name, A=A, k=k, rp=rp, ci=ci, v=v, X=Xd, Y=Yd, plan=plan, cfg=plan.config,
                               bytes=compulsory_bytes(A.m, A.n, A.nnz, k), flops=2.0 * A.nnz * k))
     stream = torch.cuda.current_stream(dev)
@@ -295,7 +328,7 @@ def run_gpu(args, rank, world, local_rank):
     L.gbs_fp64_probe(probe_out.data_ptr(), blocks, threads_p, iters, stream.cuda_stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    fp64_peak_gflops = 2.0 * 8 * iters * blocks * threads_p / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    fp64_probe_gflops = 2.0 * 8 * iters * blocks * threads_p / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
     # ---- warm-up
     for _ in range(args.warmup):
@@ -373,6 +406,11 @@ def run_gpu(args, rank, world, local_rank):
     peak_src = "measured"
     if not hbm_peak:
         hbm_peak, peak_src = 6800.0, "fallback"
+    # FP64 roof from the unit counts: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma
+    # peak_sustained = 2), 2 flops each, at the median SM clock sampled during the timed region
+    clk = sampler.summary()
+    sm_mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2070.0
+    fp64_peak_gflops = 2.0 * 2.0 * sms * sm_mhz * 1e6 / 1e9
     per = []
     for j, it in enumerate(items):
         ms = statistics.mean(per_item_ms[j])
@@ -385,10 +423,13 @@ def run_gpu(args, rank, world, local_rank):
     t_hbm = items[dom]["bytes"] / (hbm_peak * 1e9)
     t_alu = items[dom]["flops"] / (fp64_peak_gflops * 1e9)
     hbm_roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": d["hbm_frac"],
-                "traffic": None, "kernel": f"{d['matrix']} k={d['k']} {d['config']}",
+                "traffic": recorded_traffic(d["config"]["variant"], d["matrix"]) if d["k"] == 1 else None,
+                "algorithmic_bytes": items[dom]["bytes"], "kernel": f"{d['matrix']} k={d['k']} {d['config']}",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"}
     alu_roof = {"bound": "alu", "achieved": d["gflops"], "peak": fp64_peak_gflops, "unit": "GFLOP/s",
-                "frac": d["fp64_frac"], "peak_source": "FP64 FMA rate measured live in this run (gbs_fp64_probe)"}
+                "frac": d["fp64_frac"],
+                "peak_source": f"derived: 2 DFMA/clk/SM x 2 flop x {sms} SMs x {sm_mhz:.0f} MHz (median sampled clock); "
+                               f"the gbs_fp64_probe kernel reaches {fp64_probe_gflops:.0f} GFLOP/s"}
     roofline = hbm_roof
     roofline["binding_roof"] = "fp64_alu" if t_alu > t_hbm else "hbm"
     roofline["fp64_alu"] = alu_roof
@@ -407,7 +448,8 @@ def run_gpu(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "clocks": sampler.summary(),
         "gpu_launches": launches,
-        "fp64_fma_peak_gflops": fp64_peak_gflops,
+        "fp64_peak_gflops_derived": fp64_peak_gflops, "fp64_probe_gflops": fp64_probe_gflops,
+        "fp64_emulation": bool(args.emulate),
         "per_matrix": per,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -602,6 +644,9 @@ def main():
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
+    ap.add_argument("--emulate", action="store_true",
+                    help="let the tuner run part of the FP64 products on the FP32 pipe (float-float, within the "
+                         "FP64 accuracy bound); off by default, so the default line is native FP64 arithmetic")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))

@@ -67,9 +67,12 @@ typedef enum {
   GBS_VARIANT_AUTO = 0,   /* let the library choose from the row-length statistics */
   GBS_VARIANT_ROWS = 1,   /* sub-warp per row: `lanes` lanes share one row */
   GBS_VARIANT_MERGE = 2,  /* merge-path: equal shares of (rows + nonzeros) per thread */
-  GBS_VARIANT_ROWS_TMA = 3 /* ROWS with persistent CTAs and a double-buffered bulk-copy (TMA)
+  GBS_VARIANT_ROWS_TMA = 3, /* ROWS with persistent CTAs and a double-buffered bulk-copy (TMA)
                               pipeline; plans only (the plan sizes the tile to the largest
                               row block); needs 16-byte aligned vals and col_idx, else runs as ROWS */
+  GBS_VARIANT_MERGE_DIRECT = 4 /* merge-path whose threads load their own nonzeros from global
+                                  memory in 128-bit groups (no shared-memory staging of vals /
+                                  col_idx), so more items per thread fit */
 } gbs_variant;
 
 /*
@@ -81,6 +84,14 @@ typedef enum {
  *   threads      threads per CTA (multiple of 32, <= 1024).
  *   tile_nnz     ROWS: nonzeros staged in shared memory per pass.
  *   items        MERGE: merge-path items (rows + nonzeros) per thread.
+ *   emul         ROWS_TMA with double values: in every group of 4 nonzeros
+ *                a lane handles, the first `emul` (0..3) products run on the
+ *                FP32 pipe as float-float arithmetic (double operands split
+ *                into two floats by integer operations, TwoSum accumulation),
+ *                the others on the FP64 pipe, so both pipes work at once.
+ *                Each such product is accurate to about 2^-44 of |a x| and the
+ *                sums stay within 3e-13 of sum |a x| per entry; operands
+ *                outside [2^-100, 2^101) in magnitude use the FP64 pipe.
  */
 typedef struct {
   int variant;
@@ -88,6 +99,7 @@ typedef struct {
   int threads;
   int tile_nnz;
   int items;
+  int emul;
 } gbs_config;
 
 /* Row-length statistics computed on the device (gbs_csr_stats). */
@@ -198,13 +210,15 @@ int spmm_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, 
  * computes the row-length statistics, picks a configuration and owns any
  * scratch it needs.  With GBS_PLAN_TUNE it times candidate configurations
  * on the device (on scratch values it allocates itself) and keeps the
- * fastest.  With GBS_PLAN_CHECK it validates the structure first.  The plan
+ * fastest (with GBS_PLAN_EMULATE also candidates that run part of the FP64
+ * products on the FP32 pipe).  With GBS_PLAN_CHECK it validates the structure first.  The plan
  * keeps row_ptr and col_idx as given: they must stay valid and unchanged
  * while the plan is used.  gbs_plan_create synchronises `stream`.
  * Executing a plan allocates nothing and can be captured in a CUDA graph.
  */
 #define GBS_PLAN_TUNE 1
 #define GBS_PLAN_CHECK 2
+#define GBS_PLAN_EMULATE 4 /* let the tuner try FP32-pipe emulation (gbs_config.emul) for double values */
 
 typedef struct gbs_plan gbs_plan;
 

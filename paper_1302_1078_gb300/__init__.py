@@ -164,7 +164,7 @@ class Plan:
     The plan keeps references to row_ptr and col_idx; executing it allocates nothing."""
 
     def __init__(self, row_ptr, col_idx, n: int, dtype=torch.float64, k: int = 1, *, tune: bool = False,
-                 check: bool = False, config=None, stream=None):
+                 check: bool = False, emulate: bool = False, config=None, stream=None):
         _check_index(row_ptr, col_idx)
         dev = _need_cuda(row_ptr, col_idx)
         self.row_ptr, self.col_idx = row_ptr, col_idx
@@ -172,7 +172,8 @@ class Plan:
         self.dtype = dtype
         self.device = dev
         self._h = ctypes.c_void_p()
-        flags = (_capi.PLAN_TUNE if tune else 0) | (_capi.PLAN_CHECK if check else 0)
+        flags = (_capi.PLAN_TUNE if tune else 0) | (_capi.PLAN_CHECK if check else 0) | \
+            (_capi.PLAN_EMULATE if emulate else 0)
         dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
         _capi.check(lib().gbs_plan_create(ctypes.byref(self._h), self.m, self.n, self.nnz, _ptr(row_ptr),
                                           _ptr(col_idx), dt, self.k, flags, _stream(dev, stream)), "gbs_plan_create")

@@ -34,13 +34,15 @@ VARIANT_AUTO = 0
 VARIANT_ROWS = 1
 VARIANT_MERGE = 2
 VARIANT_ROWS_TMA = 3
+VARIANT_MERGE_DIRECT = 4
 
 PLAN_TUNE = 1
 PLAN_CHECK = 2
+PLAN_EMULATE = 4
 
 
 class gbs_config(ctypes.Structure):
-    _fields_ = [("variant", I32), ("lanes", I32), ("threads", I32), ("tile_nnz", I32), ("items", I32)]
+    _fields_ = [("variant", I32), ("lanes", I32), ("threads", I32), ("tile_nnz", I32), ("items", I32), ("emul", I32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -34,6 +34,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 bool valid_dtype(int d) { return d == GBS_F64 || d == GBS_F32; }
+bool is_merge(int v) { return v == GBS_VARIANT_MERGE || v == GBS_VARIANT_MERGE_DIRECT; }
 size_t dsize(int d) { return d == GBS_F64 ? 8 : 4; }
 int vec_of(int d) { return d == GBS_F64 ? 2 : 4; }
 bool pow2_lanes(int l) { return l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32; }
@@ -50,6 +51,11 @@ int check_csr(int m, int n, int nnz, const int* rp, const int* ci, const void* v
   if (nnz > 0 && (ci == nullptr || vals == nullptr)) return fail(GBS_EINVAL, "col_idx or vals is NULL");
   if ((long long)m + nnz > 0x7fffffffLL) return fail(GBS_EUNSUPPORTED, "m + nnz must be below 2^31");
   return GBS_OK;
+}
+
+bool tune_log() {
+  const char* e = std::getenv("GBSPMV_TUNE_LOG");
+  return e && e[0] && e[0] != '0';
 }
 
 bool checked_mode() {
@@ -96,15 +102,16 @@ struct MergeGeom {
 };
 
 int check_cfg(const gbs_config& c) {
-  if (c.variant != GBS_VARIANT_ROWS && c.variant != GBS_VARIANT_MERGE && c.variant != GBS_VARIANT_ROWS_TMA)
-    return fail(GBS_EINVAL, "variant must be ROWS, MERGE or ROWS_TMA after resolution");
+  if (c.variant != GBS_VARIANT_ROWS && !is_merge(c.variant) && c.variant != GBS_VARIANT_ROWS_TMA)
+    return fail(GBS_EINVAL, "variant must be ROWS, MERGE, ROWS_TMA or MERGE_DIRECT after resolution");
   if (c.variant == GBS_VARIANT_ROWS_TMA && c.threads > 256) return fail(GBS_EINVAL, "ROWS_TMA threads must be <= 256");
   if (c.threads % 32 != 0 || c.threads < 32 || c.threads > 1024) return fail(GBS_EINVAL, "threads must be 32..1024, multiple of 32");
-  if (c.variant == GBS_VARIANT_MERGE && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
+  if (is_merge(c.variant) && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
   if (c.lanes != 0 && !pow2_lanes(c.lanes)) return fail(GBS_EINVAL, "lanes must be 1, 2, 4, 8, 16 or 32");
   if ((c.variant == GBS_VARIANT_ROWS || c.variant == GBS_VARIANT_ROWS_TMA) && (c.tile_nnz < 32 || c.tile_nnz > (1 << 14)))
     return fail(GBS_EINVAL, "tile_nnz must be in [32, 16384]");
-  if (c.variant == GBS_VARIANT_MERGE && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
+  if (is_merge(c.variant) && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
+  if (c.emul < 0 || c.emul > 3) return fail(GBS_EINVAL, "emul must be in [0, 3]");
   return GBS_OK;
 }
 
@@ -167,8 +174,8 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
       int lanes = cfg.lanes;
       if (k > 1) lanes = std::max(lanes, col_lanes(kp, dtype, vec16));
       DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
-      e = dtype == GBS_F64 ? launch_rows_tma_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, status, s)
-                           : launch_rows_tma_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, status, s);
+      e = dtype == GBS_F64 ? launch_rows_tma_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, cfg.emul, status, s)
+                           : launch_rows_tma_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, status, s);
       if (e != cudaSuccess) return cuda_fail(e, "ROWS_TMA launch");
     }
     return GBS_OK;
@@ -208,8 +215,9 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
   for (int c0 = 0; rc == GBS_OK && c0 < k; c0 += P) {
     const int kp = std::min(P, k - c0);
     DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
-    e = dtype == GBS_F64 ? launch_merge_f64(A, D, g, vec16, cfg.threads, G.items, use->s, s)
-                         : launch_merge_f32(A, D, g, vec16, cfg.threads, G.items, use->s, s);
+    const bool direct = cfg.variant == GBS_VARIANT_MERGE_DIRECT;
+    e = dtype == GBS_F64 ? launch_merge_f64(A, D, g, vec16, direct, cfg.threads, G.items, use->s, s)
+                         : launch_merge_f32(A, D, g, vec16, direct, cfg.threads, G.items, use->s, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "MERGE launch");
   }
   if (use == &local) {
@@ -548,6 +556,7 @@ struct gbs_plan {
   gbs_config cfg{};
   MergeBuffers mb{};
   bool coords_ready = false;
+  int flags = 0;
   int* status = nullptr;  // device word: bounded-wait status of the pipelined variant
 };
 
@@ -575,7 +584,7 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
     p->cfg.tile_nnz = tile;
     return GBS_OK;
   }
-  if (p->cfg.variant != GBS_VARIANT_MERGE || p->m == 0) return GBS_OK;
+  if (!is_merge(p->cfg.variant) || p->m == 0) return GBS_OK;
   // the partition depends on the lanes per merge thread, which depend on whether a call
   // can use 128-bit column access; the plan is made for that case (k > 1) and calls that
   // cannot use it take the stream-ordered path
@@ -597,7 +606,7 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
 
 int plan_run(const gbs_plan* p, const void* vals, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t s) {
   CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, vals};
-  if (p->cfg.variant == GBS_VARIANT_MERGE) {
+  if (is_merge(p->cfg.variant)) {
     // the partition was made for 128-bit column access; if this call cannot use it the
     // lane count differs and the stream-ordered path is used instead
     const bool vec16 = dense_vec16(p->dtype, p->k, X, ldx, Y, ldy);
@@ -636,18 +645,35 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     }
     add(GBS_VARIANT_ROWS, 1, 128, fit_tile(128, 1), 0);
     add(GBS_VARIANT_ROWS, 2, 128, fit_tile(128, 2), 0);
-    for (int l : {1, 2, 4})
-      for (int th : {128, 256})
-        if (l == 1 || p->stats.mean_row >= 0.5 * l) add(GBS_VARIANT_ROWS_TMA, l, th, 0, 0);
+    const int tma_shapes[][2] = {{1, 32}, {1, 64}, {1, 128}, {2, 64}, {2, 128}, {2, 256}, {4, 128}, {4, 256}, {8, 256}};
+    for (const auto& sh : tma_shapes)
+      for (int l = sh[0], th = sh[1], once = 1; once; once = 0)
+        if (l == 1 || p->stats.mean_row >= 0.5 * l) {
+          add(GBS_VARIANT_ROWS_TMA, l, th, 0, 0);
+          if (p->dtype == GBS_F64 && (p->flags & GBS_PLAN_EMULATE))
+            for (int em : {1, 2}) {
+              add(GBS_VARIANT_ROWS_TMA, l, th, 0, 0);
+              c.back().emul = em;
+            }
+        }
     for (int it : {7, 11, 15, 23, 31}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
+    for (int it : {15, 23, 31, 47, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, it);
+    for (int it : {31, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 128, 0, it);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 256, base_tile / 2, 0);
     add(GBS_VARIANT_ROWS_TMA, 0, 128, 0, 0);
     add(GBS_VARIANT_ROWS_TMA, 0, 256, 0, 0);
+    if (p->dtype == GBS_F64 && (p->flags & GBS_PLAN_EMULATE))
+      for (int th : {128, 256})
+        for (int em : {1, 2, 3}) {
+          add(GBS_VARIANT_ROWS_TMA, 0, th, 0, 0);
+          c.back().emul = em;
+        }
     add(GBS_VARIANT_MERGE, 0, 256, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
+    add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, 0);
   }
   return c;
 }
@@ -690,6 +716,9 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
       }
       if (!ok) continue;
       std::sort(times, times + 3);
+      if (tune_log())
+        std::fprintf(stderr, "gbspmv tune m=%d nnz=%d k=%d: variant=%d lanes=%d threads=%d tile=%d items=%d emul=%d -> %.4f ms\n",
+                     p->m, p->nnz, p->k, c.variant, c.lanes, c.threads, p->cfg.tile_nnz, c.items, c.emul, times[1]);
       if (times[1] < best) {
         best = times[1];
         best_cfg = c;
@@ -733,6 +762,7 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   p->dtype = dtype;
   p->row_ptr = row_ptr;
   p->col_idx = col_idx;
+  p->flags = flags;
   cudaGetDevice(&p->device);
   if (cudaMalloc(reinterpret_cast<void**>(&p->status), 256) != cudaSuccess ||
       cudaMemsetAsync(p->status, 0, 256, s) != cudaSuccess) {
@@ -979,14 +1009,14 @@ constexpr int kBatchThreads = 256;
 size_t rows_smem_host(int dtype, int rpc, int tile) {
   return dtype == GBS_F64 ? rows_smem_bytes<double>(rpc, tile) : rows_smem_bytes<float>(rpc, tile);
 }
-size_t merge_smem_host(int dtype, int g, bool vec16, int items) {
+size_t merge_smem_host(int dtype, int g, bool vec16, int items, bool direct) {
   const int vec = vec16 ? vec_of(dtype) : 1;
   const int nt = kBatchThreads / g;
   const size_t es = dsize(dtype);
   const size_t ipc = (size_t)nt * items;
   size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
-  size_t b = ((ipc + 4) * es + 15) & ~(size_t)15;
-  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  size_t b = direct ? 0 : ((ipc + 4) * es + 15) & ~(size_t)15;
+  size_t c = direct ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
   return a + b + c + 2 * 32 * sizeof(int) + 2 * (size_t)kBatchThreads * vec * es;
 }
 
@@ -1012,7 +1042,7 @@ void fill_desc(gbs_batch_plan* p, int b, BatchDesc<T>* d) {
   d->items = c.items;
   d->item_begin = p->item_begin[b];
   d->nitems = p->item_begin[b + 1] - p->item_begin[b];
-  if (c.variant == GBS_VARIANT_MERGE) {
+  if (is_merge(c.variant)) {
     d->coords = p->mbs[b].s.coords;
     d->carry_row = p->mbs[b].s.carry_row;
     d->carry_val = static_cast<T*>(p->mbs[b].s.carry_val);
@@ -1163,7 +1193,7 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       const MergeGeom G = merge_geom(c, it.m, it.nnz, dtype, k, vec16);
       p->cfgs[b].items = G.items;
       nitems = it.m > 0 ? G.ctas : 0;
-      p->smem = std::max(p->smem, merge_smem_host(dtype, G.g, vec16, G.items));
+      p->smem = std::max(p->smem, merge_smem_host(dtype, G.g, vec16, G.items, c.variant == GBS_VARIANT_MERGE_DIRECT));
       scratch_off[b] = scratch_total;
       const size_t bytes = align256(merge_scratch_bytes(G.ctas, G.kp_max, dtype) + sizeof(int));
       p->mbs[b].bytes = bytes;
@@ -1181,7 +1211,7 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
     e = cudaMalloc(&p->scratch, scratch_total);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, scratch_total, s);
     for (int b = 0; b < nmat && e == cudaSuccess; ++b) {
-      if (p->cfgs[b].variant != GBS_VARIANT_MERGE) continue;
+      if (!is_merge(p->cfgs[b].variant)) continue;
       const gbs_batch_item& it = p->items[b];
       const MergeGeom G = merge_geom(p->cfgs[b], it.m, it.nnz, dtype, k, vec16);
       p->mbs[b].base = static_cast<char*>(p->scratch) + scratch_off[b];
@@ -1273,7 +1303,7 @@ int spmv_csr_batched_looped(gbs_batch_plan* p, void* stream) {
     if (c.variant == GBS_VARIANT_ROWS && p->k > 1) c.lanes = p->G;
     MergeBuffers mb = p->mbs[b];
     int rc = run_product(A, p->dtype, p->k, it.X, p->k == 1 ? 1 : it.ldx, it.Y, p->k == 1 ? 1 : it.ldy, c,
-                         c.variant == GBS_VARIANT_MERGE ? &mb : nullptr, true, s);
+                         is_merge(c.variant) ? &mb : nullptr, true, s);
     if (rc) return rc;
   }
   return GBS_OK;

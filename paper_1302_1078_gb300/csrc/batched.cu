@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchDesc<T>* __rest
       }
     } else {
       const MergeArgs<T> a = merge_args(d);
-      merge_tile<T, VEC, (SPLIT ? 1 : G)>(a, local);
+      merge_tile<T, VEC, (SPLIT ? 1 : G), false>(a, local);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();  // this tile's Y rows and carry are visible before it is counted

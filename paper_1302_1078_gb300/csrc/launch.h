@@ -38,18 +38,20 @@ cudaError_t launch_rows_f32(const CsrView& A, const DenseView& D, int lanes, boo
 
 // ROWS_TMA variant (persistent, bulk-copy pipeline).  tile must hold the largest block's
 // nonzeros + 8; vals and col_idx 16-byte aligned; status: device int (bit 0 = wait timeout).
+// emul (FP64 only, 0..3): products per group of 4 nonzeros computed on the FP32 pipe (df64.cuh).
 cudaError_t launch_rows_tma_f64(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
-                                int* status, cudaStream_t s);
+                                int emul, int* status, cudaStream_t s);
 cudaError_t launch_rows_tma_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
-                                int* status, cudaStream_t s);
+                                int emul, int* status, cudaStream_t s);
 size_t rows_tma_smem(int dtype, int rows_per_cta, int tile);
 
 // MERGE variant: partition (coords) must have been computed for (threads / g) * items
-// items per CTA.  g lanes per merge thread (columns), g * VEC >= k.
-cudaError_t launch_merge_f64(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
-                             const MergeScratch& S, cudaStream_t s);
-cudaError_t launch_merge_f32(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
-                             const MergeScratch& S, cudaStream_t s);
+// items per CTA.  g lanes per merge thread (columns), g * VEC >= k.  direct: each merge
+// thread loads its nonzeros from global memory (MERGE_DIRECT) instead of shared memory.
+cudaError_t launch_merge_f64(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
+                             int items, const MergeScratch& S, cudaStream_t s);
+cudaError_t launch_merge_f32(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
+                             int items, const MergeScratch& S, cudaStream_t s);
 cudaError_t launch_merge_partition(const CsrView& A, long long items_per_cta, const MergeScratch& S, cudaStream_t s);
 
 // Exclusive prefix sum of int32 (in == out allowed); ws holds scan_workspace_ints(count) ints.

@@ -67,10 +67,10 @@ cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool 
   }
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT>
+template <typename T, int VEC, int LANES, bool SPLIT, int EMUL>
 static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* status, int threads, size_t smem,
                                cudaStream_t s) {
-  auto kern = rows_tma_kernel<T, VEC, LANES, SPLIT>;
+  auto kern = rows_tma_kernel<T, VEC, LANES, SPLIT, EMUL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int bps = 0, dev = 0, sms = 0;
@@ -83,18 +83,32 @@ static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* 
   return cudaGetLastError();
 }
 
+template <typename T, int VEC, int LANES, bool SPLIT>
+static cudaError_t rows_tma_emul(const RowsArgs<T>& a, int emul, int nblocks, int nnz, int* status, int threads,
+                                 size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    switch (emul) {
+      case 1: return rows_tma_go<T, VEC, LANES, SPLIT, 1>(a, nblocks, nnz, status, threads, smem, s);
+      case 2: return rows_tma_go<T, VEC, LANES, SPLIT, 2>(a, nblocks, nnz, status, threads, smem, s);
+      case 3: return rows_tma_go<T, VEC, LANES, SPLIT, 3>(a, nblocks, nnz, status, threads, smem, s);
+      default: break;
+    }
+  }
+  return rows_tma_go<T, VEC, LANES, SPLIT, 0>(a, nblocks, nnz, status, threads, smem, s);
+}
+
 template <typename T, int LANES>
-static cudaError_t rows_tma_lanes(const RowsArgs<T>& a, bool split, bool vec16, int nblocks, int nnz, int* status,
-                                  int threads, size_t smem, cudaStream_t s) {
+static cudaError_t rows_tma_lanes(const RowsArgs<T>& a, bool split, bool vec16, int emul, int nblocks, int nnz,
+                                  int* status, int threads, size_t smem, cudaStream_t s) {
   constexpr int V = 16 / (int)sizeof(T);
-  if (split) return rows_tma_go<T, 1, LANES, true>(a, nblocks, nnz, status, threads, smem, s);
-  if (vec16) return rows_tma_go<T, V, LANES, false>(a, nblocks, nnz, status, threads, smem, s);
-  return rows_tma_go<T, 1, LANES, false>(a, nblocks, nnz, status, threads, smem, s);
+  if (split) return rows_tma_emul<T, 1, LANES, true>(a, emul, nblocks, nnz, status, threads, smem, s);
+  if (vec16) return rows_tma_emul<T, V, LANES, false>(a, emul, nblocks, nnz, status, threads, smem, s);
+  return rows_tma_emul<T, 1, LANES, false>(a, emul, nblocks, nnz, status, threads, smem, s);
 }
 
 template <typename T>
 cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
-                              int* status, cudaStream_t s) {
+                              int emul, int* status, cudaStream_t s) {
   if (A.m <= 0) return cudaSuccess;
   RowsArgs<T> a;
   a.m = A.m;
@@ -115,20 +129,20 @@ cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, b
   const size_t smem = rows_tma_smem_bytes<T>(rpc, tile);
   const bool split = D.k == 1;
   switch (lanes) {
-    case 1: return rows_tma_lanes<T, 1>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
-    case 2: return rows_tma_lanes<T, 2>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
-    case 4: return rows_tma_lanes<T, 4>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
-    case 8: return rows_tma_lanes<T, 8>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
-    case 16: return rows_tma_lanes<T, 16>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
-    case 32: return rows_tma_lanes<T, 32>(a, split, vec16, nblocks, A.nnz, status, threads, smem, s);
+    case 1: return rows_tma_lanes<T, 1>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
+    case 2: return rows_tma_lanes<T, 2>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
+    case 4: return rows_tma_lanes<T, 4>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
+    case 8: return rows_tma_lanes<T, 8>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
+    case 16: return rows_tma_lanes<T, 16>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
+    case 32: return rows_tma_lanes<T, 32>(a, split, vec16, emul, nblocks, A.nnz, status, threads, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, int VEC, int G>
+template <typename T, int VEC, int G, bool DIRECT>
 static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
-  auto kern = merge_kernel<T, VEC, G>;
-  const size_t smem = merge_smem_bytes<T, VEC, G>(threads, a.items);
+  auto kern = merge_kernel<T, VEC, G, DIRECT>;
+  const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<a.ctas, threads, smem, s>>>(a);
@@ -139,15 +153,19 @@ static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) 
 }
 
 template <typename T, int G>
-static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, int threads, cudaStream_t s) {
+static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, bool direct, int threads, cudaStream_t s) {
   constexpr int V = 16 / (int)sizeof(T);
-  if (vec16 && a.k > 1) return merge_go<T, V, G>(a, threads, s);
-  return merge_go<T, 1, G>(a, threads, s);
+  if (direct) {
+    if (vec16 && a.k > 1) return merge_go<T, V, G, true>(a, threads, s);
+    return merge_go<T, 1, G, true>(a, threads, s);
+  }
+  if (vec16 && a.k > 1) return merge_go<T, V, G, false>(a, threads, s);
+  return merge_go<T, 1, G, false>(a, threads, s);
 }
 
 template <typename T>
-cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec16, int threads, int items,
-                           const MergeScratch& S, cudaStream_t s) {
+cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
+                           int items, const MergeScratch& S, cudaStream_t s) {
   if (A.m == 0) return cudaSuccess;
   MergeArgs<T> a;
   a.m = A.m;
@@ -168,26 +186,26 @@ cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec
   a.aligned_vals = (reinterpret_cast<uintptr_t>(A.vals) & 15) == 0;
   a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
   switch (g) {
-    case 1: return merge_g<T, 1>(a, vec16, threads, s);
-    case 2: return merge_g<T, 2>(a, vec16, threads, s);
-    case 4: return merge_g<T, 4>(a, vec16, threads, s);
-    case 8: return merge_g<T, 8>(a, vec16, threads, s);
-    case 16: return merge_g<T, 16>(a, vec16, threads, s);
-    case 32: return merge_g<T, 32>(a, vec16, threads, s);
+    case 1: return merge_g<T, 1>(a, vec16, direct, threads, s);
+    case 2: return merge_g<T, 2>(a, vec16, direct, threads, s);
+    case 4: return merge_g<T, 4>(a, vec16, direct, threads, s);
+    case 8: return merge_g<T, 8>(a, vec16, direct, threads, s);
+    case 16: return merge_g<T, 16>(a, vec16, direct, threads, s);
+    case 32: return merge_g<T, 32>(a, vec16, direct, threads, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
-size_t merge_smem_t(int g, bool vec16, int threads, int items) {
+size_t merge_smem_t(int g, bool vec16, bool direct, int threads, int items) {
   constexpr int V = 16 / (int)sizeof(T);
   const int vec = vec16 ? V : 1;
   // same formula for every G: s_cval holds threads * vec elements
   const int nt = threads / g;
   const size_t ipc = (size_t)nt * items;
   size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
-  size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
-  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  size_t b = direct ? 0 : ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
+  size_t c = direct ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
   size_t d = 2 * 32 * sizeof(int);
   size_t e = 2 * (size_t)threads * vec * sizeof(T);
   return a + b + c + d + e;

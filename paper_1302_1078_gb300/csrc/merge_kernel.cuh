@@ -26,6 +26,13 @@
 //   * A group of G lanes shares one merge thread; each lane owns VEC of the
 //     k columns (SpMM), so the X row of a nonzero is gathered with G
 //     coalesced 128-bit loads.
+//   * Two ways to fetch the nonzeros (template DIRECT): the CTA stages the
+//     tile's vals / col_idx in shared memory with coalesced loads (MERGE), or
+//     each merge thread reads its own contiguous segment straight from
+//     global memory in aligned 128-bit groups of four (MERGE_DIRECT).  The
+//     direct form needs only the row-pointer window in shared memory (4 bytes
+//     per item instead of 16), which allows more items per thread at the same
+//     residency and spreads the carry scan over more nonzeros.
 #pragma once
 #include "device_common.cuh"
 
@@ -65,13 +72,13 @@ __device__ __forceinline__ int2 merge_search_global(const int* __restrict__ row_
   return make_int2((int)lo, (int)(d - lo));
 }
 
-template <typename T, int VEC, int G>
+template <typename T, int VEC, int G, bool DIRECT = false>
 __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
   int nt = threads / G;
   size_t ipc = (size_t)nt * items;
   size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;           // s_rp
-  size_t b = ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;             // s_val
-  size_t c = ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;           // s_col
+  size_t b = DIRECT ? 0 : ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;  // s_val
+  size_t c = DIRECT ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;  // s_col
   size_t d = 2 * 32 * sizeof(int);                                   // s_wkey, s_cinkey
   size_t e = 2 * (size_t)threads * VEC * sizeof(T);                  // s_wval, s_cinval (per warp: 32 lanes x VEC)
   return a + b + c + d + e;
@@ -79,7 +86,7 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
 
 // One merge-path tile b of the product (the whole CTA works on it).  Used by the
 // standalone kernel below and by the batched persistent kernel.
-template <typename T, int VEC, int G>
+template <typename T, int VEC, int G, bool DIRECT = false>
 __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = blockDim.x / G;
@@ -93,9 +100,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   int* s_rp = reinterpret_cast<int*>(smem_raw);
   size_t off = (((size_t)ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
   T* s_val = reinterpret_cast<T*>(smem_raw + off);
-  off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
+  if (!DIRECT) off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
   int* s_col = reinterpret_cast<int*>(smem_raw + off);
-  off += (((size_t)ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
+  if (!DIRECT) off += (((size_t)ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
   int* s_wkey = reinterpret_cast<int*>(smem_raw + off);
   int* s_cinkey = s_wkey + 32;
   off += 2 * 32 * sizeof(int);
@@ -110,7 +117,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   const int nrp = rlast >= row0 ? rlast - row0 + 2 : 0;
   for (int q = threadIdx.x; q < nrp; q += blockDim.x) s_rp[q] = ld_stream(a.row_ptr + row0 + q, pol_stream);
   const int a0 = nz0 & ~3;
-  if (nz1 > nz0) {
+  if (!DIRECT && nz1 > nz0) {
     stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
     stage_copy<int>(s_col, a.col_idx, a0, nz1, a.aligned_cols, pol_stream);
   }
@@ -177,6 +184,74 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     for (int j = 0; j < VEC; ++j) acc[j].reset();
   };
 
+  if constexpr (DIRECT) {
+    // each merge thread streams its own contiguous segment [nz_s, nz_e) from global memory:
+    // scalar up to a multiple of 4, then aligned 128-bit groups of four, then the tail
+    auto gather = [&](int c) {
+      Vec<T, VEC> xv;
+      if (col_full) {
+        xv = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) xv.v[j] = (c_lo + j < a.k) ? ld_keep(Xc + (long long)c * a.ldx + j, pol_keep) : T(0);
+      }
+      return xv;
+    };
+    auto one = [&](int q) {
+      const T vv = ld_stream(a.vals + q, pol_stream);
+      const int cc = ld_stream(a.col_idx + q, pol_stream);
+      Vec<T, VEC> xv;
+      if (col_active) xv = gather(cc);
+      while (row < row_e && s_rp[row - row0 + 1] <= q) {
+        emit(row);
+        ++row;
+      }
+      if (col_active) {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) acc[j].add(vv, xv.v[j]);
+      }
+    };
+    int nz = nz_s;
+    if (a.aligned_vals && a.aligned_cols) {
+      for (; nz < nz_e && (nz & 3); ++nz) one(nz);
+      for (; nz + 4 <= nz_e; nz += 4) {
+        T v[4];
+        if constexpr (sizeof(T) == 8) {
+          const uint4 w0 = ld_stream_v4(a.vals + nz, pol_stream);
+          const uint4 w1 = ld_stream_v4(a.vals + nz + 2, pol_stream);
+          v[0] = __hiloint2double((int)w0.y, (int)w0.x);
+          v[1] = __hiloint2double((int)w0.w, (int)w0.z);
+          v[2] = __hiloint2double((int)w1.y, (int)w1.x);
+          v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+        } else {
+          const uint4 w = ld_stream_v4(a.vals + nz, pol_stream);
+          v[0] = __uint_as_float(w.x);
+          v[1] = __uint_as_float(w.y);
+          v[2] = __uint_as_float(w.z);
+          v[3] = __uint_as_float(w.w);
+        }
+        const uint4 cw = ld_stream_v4(a.col_idx + nz, pol_stream);
+        const int c4[4] = {(int)cw.x, (int)cw.y, (int)cw.z, (int)cw.w};
+        Vec<T, VEC> xv[4];
+        if (col_active) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) xv[u] = gather(c4[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          while (row < row_e && s_rp[row - row0 + 1] <= nz + u) {
+            emit(row);
+            ++row;
+          }
+          if (col_active) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+          }
+        }
+      }
+    }
+    for (; nz < nz_e; ++nz) one(nz);
+  } else {
   constexpr int U = 4;
   for (int nz = nz_s; nz < nz_e; nz += U) {
     const int cnt = min(U, nz_e - nz);
@@ -209,6 +284,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       }
     }
   }
+  }  // staged
   while (row < row_e) {
     emit(row);
     ++row;
@@ -300,9 +376,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   }
 }
 
-template <typename T, int VEC, int G>
+template <typename T, int VEC, int G, bool DIRECT>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
-  merge_tile<T, VEC, G>(a, blockIdx.x);
+  merge_tile<T, VEC, G, DIRECT>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of

@@ -119,8 +119,8 @@ extern "C" int spmv_csr_noalloc(int m, int n, int nnz, const int* row_ptr, const
   DenseView D{1, x, 1, y, 1};
   cudaError_t e = launch_merge_partition(A, ipc, S, s);
   if (e == cudaSuccess)
-    e = dtype == GBS_F64 ? launch_merge_f64(A, D, 1, false, kNoAllocThreads, kNoAllocItems, S, s)
-                         : launch_merge_f32(A, D, 1, false, kNoAllocThreads, kNoAllocItems, S, s);
+    e = dtype == GBS_F64 ? launch_merge_f64(A, D, 1, false, false, kNoAllocThreads, kNoAllocItems, S, s)
+                         : launch_merge_f32(A, D, 1, false, false, kNoAllocThreads, kNoAllocItems, S, s);
   if (e != cudaSuccess) {
     set_last_error((std::string("spmv_csr_noalloc launch: ") + cudaGetErrorString(e)).c_str());
     return GBS_ECUDA;

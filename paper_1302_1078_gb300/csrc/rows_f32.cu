@@ -6,8 +6,4 @@ cudaError_t launch_rows_f32(const CsrView& A, const DenseView& D, int lanes, boo
                            int row_base, int rows, cudaStream_t s) {
   return launch_rows_t<float>(A, D, lanes, vec16, threads, tile, row_base, rows, s);
 }
-cudaError_t launch_rows_tma_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
-                               int* status, cudaStream_t s) {
-  return launch_rows_tma_t<float>(A, D, lanes, vec16, threads, tile, status, s);
-}
 }  // namespace gbs

@@ -19,7 +19,14 @@
 //
 // Every wait is bounded: on timeout the kernel sets the device error flag,
 // waits (again bounded) for the copies it issued, and returns.
+//
+// EMUL (FP64 only): in every unrolled group of 4 nonzeros, the first EMUL
+// products run on the FP32 pipe (df64.cuh) and the rest on the FP64 pipe.
+// The choice depends only on the loop position, so it is warp-uniform and
+// never masks an FP64 instruction.  The float-float partial sums are flushed
+// into the double accumulator every 16 groups (at most 48 terms).
 #pragma once
+#include "df64.cuh"
 #include "device_common.cuh"
 #include "rows_kernel.cuh"
 
@@ -76,8 +83,9 @@ __host__ __device__ inline size_t rows_tma_smem_bytes(int rpc, int tile) {
   return bars + rp + 2 * (val + col);
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT>
+template <typename T, int VEC, int LANES, bool SPLIT, int EMUL>
 __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblocks, int nnz, int* __restrict__ status) {
+  static_assert(EMUL == 0 || sizeof(T) == 8, "FP32-pipe emulation is for double values");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpc = blockDim.x / LANES;
   const int tile = a.tile;
@@ -154,6 +162,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
   const bool col_full = SPLIT ? true : (c_lo + VEC <= a.k);
   const T* __restrict__ Xc = a.X + c_lo;
   __shared__ int s_abort;
+  __shared__ T s_red[SPLIT && LANES > 1 ? 256 : 1];
   if (tid == 0) s_abort = 0;
   __syncthreads();
 
@@ -189,11 +198,13 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
     // ---- compute the rows of block blk from stage st
     const bool active = g < nr;
     Acc<T> acc[VEC];
+    DFAcc eacc[EMUL > 0 ? VEC : 1];
     if (active && col_active) {
       const int rs = rp[g], re = rp[g + 1];
       constexpr int STEP = SPLIT ? LANES : 1;
       int p = rs + (SPLIT ? lane : 0);
       if (col_full) {
+        int groups = 0;
         for (; p + (kUnroll - 1) * STEP < re; p += kUnroll * STEP) {
           T v[kUnroll];
           int c[kUnroll];
@@ -206,9 +217,40 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u)
+          for (int u = 0; u < kUnroll; ++u) {
+            if constexpr (EMUL > 0) {
+              if (u < EMUL) {
+                float ah, al;
+                const bool oka = split_f64((double)v[u], ah, al);
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                  float xh, xl;
+                  const bool okx = split_f64((double)xv[u].v[j], xh, xl);
+                  if (oka && okx)
+                    eacc[j].add(ah, al, xh, xl);
+                  else
+                    acc[j].add(v[u], xv[u].v[j]);  // out of the FP32 range: native pipe
+                }
+                continue;
+              }
+            }
 #pragma unroll
             for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+          }
+          if constexpr (EMUL > 0) {
+            if (++groups == 16) {
+              groups = 0;
+#pragma unroll
+              for (int j = 0; j < VEC; ++j) {
+                acc[j].add_partial((T)eacc[j].value());
+                eacc[j].reset();
+              }
+            }
+          }
+        }
+        if constexpr (EMUL > 0) {
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) acc[j].add_partial((T)eacc[j].value());
         }
         for (; p < re; p += STEP) {
           Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p - a0] * a.ldx, pol_keep);
@@ -226,11 +268,20 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
       }
     }
     const int r0 = blk * rpc;
-    if constexpr (SPLIT) {
-      T sum = acc[0].value();
+    if constexpr (SPLIT && LANES > 1) {
+      // transposed reduction: the LANES partials of a row go through shared memory and
+      // one thread per row adds them in lane order, so a warp of rows shares each FP64
+      // add instead of every lane paying log2(LANES) shuffled adds
+      s_red[tid] = acc[0].value();
+      __syncthreads();
+      if (tid < nr) {
+        T sum = s_red[tid * LANES];
 #pragma unroll
-      for (int o = LANES / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, LANES);
-      if (active && lane == 0) st_stream(a.Y + (long long)(r0 + g) * a.ldy, sum);
+        for (int l = 1; l < LANES; ++l) sum += s_red[tid * LANES + l];
+        st_stream(a.Y + (long long)(r0 + tid) * a.ldy, sum);
+      }
+    } else if constexpr (SPLIT) {
+      if (active) st_stream(a.Y + (long long)(r0 + g) * a.ldy, acc[0].value());
     } else {
       if (active && col_active) {
         T out[VEC];

@@ -94,7 +94,9 @@ CONFIGS = [None,
            dict(variant=1, lanes=16), dict(variant=1, lanes=32),
            dict(variant=1, lanes=1, threads=64, tile_nnz=64), dict(variant=1, lanes=4, threads=128, tile_nnz=100),
            dict(variant=2, items=1), dict(variant=2, items=4), dict(variant=2, items=16, threads=64),
-           dict(variant=2, items=7, threads=96)]
+           dict(variant=2, items=7, threads=96),
+           dict(variant=4, items=1), dict(variant=4, items=5), dict(variant=4, items=31),
+           dict(variant=4, items=63, threads=128), dict(variant=4, items=9, threads=96)]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
@@ -127,7 +129,7 @@ def test_spmm_parity(gbs, name, k, dtype):
     Xd_wide = torch.from_numpy(Xw).cuda()
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     for cfg in [None, dict(variant=1), dict(variant=1, threads=128, tile_nnz=500), dict(variant=2),
-                dict(variant=2, items=3, threads=128)]:
+                dict(variant=2, items=3, threads=128), dict(variant=4), dict(variant=4, items=13, threads=128)]:
         for XX in (Xd, Xd_wide[:, :k]):
             Y = torch.full((A.m, k), float("nan"), dtype=dtype, device="cuda")
             gbs.spmm_csr(rp, ci, v, XX, Y, config=cfg)
@@ -319,3 +321,82 @@ def test_rows_tma_refuses_huge_blocks(gbs):
     with pytest.raises(gbs.GbsError) as e:
         plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, lanes=1, threads=256))
     assert e.value.status == _capi.GBS_EUNSUPPORTED
+
+
+# ---------------------------------------- FP64 products on the FP32 pipe (emul)
+
+@pytest.mark.parametrize("emul", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 8, 16])
+@pytest.mark.parametrize("name", ["stencil3d_21", "banded_30k", "rmat_14", "random_rect", "one_row"])
+def test_rows_tma_emulated_fp64(gbs, name, k, emul):
+    from paper_1302_1078_gb300 import _capi
+
+    A = matrix(name)
+    rp, ci, v = dev_csr(A)
+    X = synth.uniform(A.n * k, seed=13, stream=k).reshape(A.n, k)
+    if k == 1:
+        Y_ref, R = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, X[:, 0])
+    else:
+        Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals, X)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, k)
+    for shape in (dict(lanes=1, threads=128), dict(lanes=2, threads=256), dict(lanes=4, threads=128)):
+        try:
+            plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, emul=emul, **shape))
+        except gbs.GbsError as e:
+            assert e.status == _capi.GBS_EUNSUPPORTED
+            continue
+        assert plan.config["emul"] == emul
+        if k == 1:
+            out = plan.spmv(v, torch.from_numpy(np.ascontiguousarray(X[:, 0])).cuda())
+        else:
+            out = plan.spmm(v, torch.from_numpy(X).cuda())
+        assert_close(out, Y_ref, R, torch.float64, f"{name} k={k} emul={emul} {shape}")
+
+
+def test_emulated_fp64_extreme_magnitudes(gbs):
+    """Operands outside the FP32 exponent range (and zeros, subnormals) take the native pipe
+    inside the emulated kernel; every entry still meets the FP64 bound."""
+    from paper_1302_1078_gb300 import _capi
+
+    rng = np.random.default_rng(17)
+    m, n, per = 2000, 3000, 24
+    rp = np.arange(0, m * per + 1, per, dtype=np.int32)
+    ci = np.sort(rng.integers(0, n, (m, per)), axis=1).astype(np.int32).reshape(-1)
+    vmags = np.array([1.0, 1e-200, 1e200, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5], np.float64)
+    xmags = np.array([1.0, 1e-200, 1e100, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5], np.float64)  # products stay finite
+    v = rng.uniform(-1, 1, m * per) * vmags[rng.integers(0, vmags.size, m * per)]
+    x = rng.uniform(-1, 1, n) * xmags[rng.integers(0, xmags.size, n)]
+    A = synth.CSR(m, n, rp, ci, v)
+    y_ref, r = oracle.spmv(m, rp, ci, v, x)
+    d_rp, d_ci, d_v = dev_csr(A)
+    plan = gbs.Plan(d_rp, d_ci, n, torch.float64, 1)
+    for emul in (0, 1, 2, 3):
+        plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, lanes=1, threads=128, emul=emul))
+        y = plan.spmv(d_v, torch.from_numpy(x).cuda())
+        assert_close(y, y_ref, r, torch.float64, f"extreme magnitudes emul={emul}")
+
+
+def test_tuner_with_emulation(gbs):
+    A = matrix("banded_30k")
+    rp, ci, v = dev_csr(A)
+    x = synth.uniform(A.n, seed=23)
+    y_ref, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, 1, tune=True, emulate=True)
+    y = plan.spmv(v, torch.from_numpy(x).cuda())
+    assert_close(y, y_ref, r, torch.float64, f"tuned with emulation {plan.config}")
+
+
+def test_merge_direct_misaligned_values(gbs):
+    """MERGE_DIRECT with vals / col_idx off a 16-byte boundary takes its scalar path."""
+    A = matrix("rmat_14")
+    rp, ci, v = dev_csr(A)
+    x = synth.uniform(A.n, seed=29)
+    y_ref, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+    vb = torch.empty(v.numel() + 2, dtype=torch.float64, device="cuda")
+    cb = torch.empty(ci.numel() + 2, dtype=torch.int32, device="cuda")
+    vm, cm = vb[1:1 + v.numel()], cb[1:1 + ci.numel()]
+    vm.copy_(v)
+    cm.copy_(ci)
+    for items in (3, 31):
+        y = gbs.spmv_csr(rp, cm, vm, torch.from_numpy(x).cuda(), config=dict(variant=4, items=items))
+        assert_close(y, y_ref, r, torch.float64, f"misaligned direct items={items}")
