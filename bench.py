@@ -80,6 +80,7 @@ KERNEL_SOURCES = {
     1: ["rows_kernel.cuh", "device_common.cuh"],
     2: ["merge_kernel.cuh", "device_common.cuh"],
     3: ["rows_tma.cuh", "rows_kernel.cuh", "device_common.cuh", "df64.cuh"],
+    4: ["merge_kernel.cuh", "device_common.cuh"],
 }
 
 
