@@ -260,6 +260,13 @@ int gbs_tplan_arrays(const gbs_tplan* plan, const int** rowptrT, const int** col
 /* Copy the plan's arrays into caller buffers (device or host, cudaMemcpyDefault), async on `stream`. */
 int gbs_tplan_export(const gbs_tplan* plan, int* rowptrT, int* colT, int* perm, void* stream);
 int gbs_tplan_destroy(gbs_tplan* plan);
+/*
+ * Make (and keep) a plan of A^T for `dtype` and k, with gbs_plan_create's
+ * flags (GBS_PLAN_TUNE to autotune it); spmv_csr_backward then computes dX with
+ * that plan's configuration instead of the one picked from A^T's row
+ * statistics.  Synchronises `stream`.  Idempotent per (dtype, k).
+ */
+int gbs_tplan_prepare(gbs_tplan* plan, int dtype, int k, int flags, void* stream);
 
 /*
  * Backward of Y = A X (k >= 1 columns; k == 1 is SpMV) for a loss L with

@@ -258,6 +258,12 @@ class TransposePlan:
                     "gbs_tplan_export")
         return rpT, ciT, perm
 
+    def prepare(self, dtype, k: int, tune: bool = True, stream=None):
+        """Make a (tuned) plan of A^T for dtype and k; later backward calls use it for dX."""
+        dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
+        _capi.check(lib().gbs_tplan_prepare(self._h, dt, int(k), _capi.PLAN_TUNE if tune else 0,
+                                            _stream(self.device, stream)), "gbs_tplan_prepare")
+
     def backward(self, vals, X, dY, need_dX: bool = True, need_dvals: bool = True, stream=None):
         """(dX, dvals) of Y = A X for upstream dY; X and dY are 1-D (SpMV) or 2-D row major."""
         _need_cuda(vals, X, dY)
@@ -295,6 +301,7 @@ class CsrOperator:
         self.tune = tune
         self._plans = {}
         self._tplan = None
+        self._prepared = set()
 
     def plan(self, dtype, k):
         key = (dtype, k)
@@ -331,7 +338,12 @@ class SpMMFunction(torch.autograd.Function):
     def backward(ctx, dY):
         vals, X = ctx.saved_tensors
         need_v, need_x = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        dX, dvals = ctx.op.tplan.backward(vals, X, dY, need_dX=need_x, need_dvals=need_v)
+        op = ctx.op
+        k = 1 if X.dim() == 1 else X.shape[1]
+        if need_x and op.tune and (vals.dtype, k) not in op._prepared:
+            op.tplan.prepare(vals.dtype, k, tune=True)
+            op._prepared.add((vals.dtype, k))
+        dX, dvals = op.tplan.backward(vals, X, dY, need_dX=need_x, need_dvals=need_v)
         return dvals, dX, None
 
 

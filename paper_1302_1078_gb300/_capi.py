@@ -83,6 +83,7 @@ SIGNATURES = {
     "gbs_tplan_arrays": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
     "gbs_tplan_export": (I32, [P, P, P, P, P]),
     "gbs_tplan_destroy": (I32, [P]),
+    "gbs_tplan_prepare": (I32, [P, I32, I32, I32, P]),
     "spmv_csr_backward": (I32, [P, P, P, P, I32, I32, P, I32, P, I32, P, I32, P, P]),
 }
 

@@ -851,6 +851,11 @@ struct gbs_tplan {
   void* valsT = nullptr; // nnz doubles (scratch for the permuted values)
   void* base = nullptr;
   gbs_stats statsT{};
+  struct Prepared {
+    int dtype, k;
+    gbs_plan* plan;
+  };
+  std::vector<Prepared> plans;  // plans of A^T, one per (dtype, k), made by gbs_tplan_prepare
 };
 
 namespace {
@@ -948,8 +953,22 @@ int gbs_tplan_export(const gbs_tplan* t, int* rowptrT, int* colT, int* perm, voi
 
 int gbs_tplan_destroy(gbs_tplan* t) {
   if (!t) return GBS_OK;
+  for (auto& pp : t->plans) gbs_plan_destroy(pp.plan);
   if (t->base) cudaFree(t->base);
   delete t;
+  return GBS_OK;
+}
+
+int gbs_tplan_prepare(gbs_tplan* t, int dtype, int k, int flags, void* stream) {
+  if (!t) return fail(GBS_EINVAL, "plan is NULL");
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  for (auto& pp : t->plans)
+    if (pp.dtype == dtype && pp.k == k) return GBS_OK;
+  gbs_plan* p = nullptr;
+  int rc = gbs_plan_create(&p, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, flags & ~GBS_PLAN_CHECK, stream);
+  if (rc) return rc;
+  t->plans.push_back({dtype, k, p});
   return GBS_OK;
 }
 
@@ -969,9 +988,17 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
     // dX = A^T dY through the precomputed transpose: values permuted once per call
     e = gather_values(dtype, vals, t->perm, t->nnz, t->valsT, s);
     if (e != cudaSuccess) return cuda_fail(e, "gather of A^T values");
-    CsrView AT{t->n, t->m, t->nnz, t->rptrT, t->colT, t->valsT};
-    gbs_config c = heuristic_config(t->statsT, dtype, k);
-    int rc = run_product(AT, dtype, k, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, c, nullptr, false, s);
+    const gbs_plan* prepared = nullptr;
+    for (auto& pp : t->plans)
+      if (pp.dtype == dtype && pp.k == k) prepared = pp.plan;
+    int rc;
+    if (prepared) {
+      rc = plan_run(prepared, t->valsT, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, s);
+    } else {
+      CsrView AT{t->n, t->m, t->nnz, t->rptrT, t->colT, t->valsT};
+      gbs_config c = heuristic_config(t->statsT, dtype, k);
+      rc = run_product(AT, dtype, k, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, c, nullptr, false, s);
+    }
     if (rc) return rc;
   }
   if (dvals) {

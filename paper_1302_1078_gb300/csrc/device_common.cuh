@@ -50,6 +50,16 @@ __device__ __forceinline__ float ld_stream(const float* ptr, uint64_t pol) {
 }
 __device__ __forceinline__ int ld_stream(const int* ptr, uint64_t pol) { return ld_stream_i32(ptr, pol); }
 
+// ---- streaming loads that do allocate in L1 (for per-thread contiguous segments whose
+//      16-byte loads each use half of a 32-byte sector: the other half then hits L1)
+__device__ __forceinline__ uint4 ld_stream_l1_v4(const void* ptr, uint64_t pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(ptr), "l"(pol));
+  return r;
+}
+
 // ---- gathers of the dense operand (reused): L2 evict-last
 __device__ __forceinline__ double ld_keep(const double* ptr, uint64_t pol) {
   double r;

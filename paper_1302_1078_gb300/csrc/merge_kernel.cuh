@@ -217,20 +217,20 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       for (; nz + 4 <= nz_e; nz += 4) {
         T v[4];
         if constexpr (sizeof(T) == 8) {
-          const uint4 w0 = ld_stream_v4(a.vals + nz, pol_stream);
-          const uint4 w1 = ld_stream_v4(a.vals + nz + 2, pol_stream);
+          const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
+          const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
           v[0] = __hiloint2double((int)w0.y, (int)w0.x);
           v[1] = __hiloint2double((int)w0.w, (int)w0.z);
           v[2] = __hiloint2double((int)w1.y, (int)w1.x);
           v[3] = __hiloint2double((int)w1.w, (int)w1.z);
         } else {
-          const uint4 w = ld_stream_v4(a.vals + nz, pol_stream);
+          const uint4 w = ld_stream_l1_v4(a.vals + nz, pol_stream);
           v[0] = __uint_as_float(w.x);
           v[1] = __uint_as_float(w.y);
           v[2] = __uint_as_float(w.z);
           v[3] = __uint_as_float(w.w);
         }
-        const uint4 cw = ld_stream_v4(a.col_idx + nz, pol_stream);
+        const uint4 cw = ld_stream_l1_v4(a.col_idx + nz, pol_stream);
         const int c4[4] = {(int)cw.x, (int)cw.y, (int)cw.z, (int)cw.w};
         Vec<T, VEC> xv[4];
         if (col_active) {

@@ -63,10 +63,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// Bulk copy global -> shared, completing on `bar`, with an L2 eviction policy (the matrix
+// streams are read once: evict-first keeps the gathered vector resident in L2).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t pol) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
       : "memory");
 }
 
@@ -135,8 +139,8 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[st], nv * (uint32_t)(sizeof(T) + sizeof(int)));
     if (nv) {
-      bulk_copy_g2s(s_val(st), a.vals + a0, nv * (uint32_t)sizeof(T), &bars[st]);
-      bulk_copy_g2s(s_col(st), a.col_idx + a0, nv * (uint32_t)sizeof(int), &bars[st]);
+      bulk_copy_g2s(s_val(st), a.vals + a0, nv * (uint32_t)sizeof(T), &bars[st], pol_stream);
+      bulk_copy_g2s(s_col(st), a.col_idx + a0, nv * (uint32_t)sizeof(int), &bars[st], pol_stream);
     }
   };
 
