@@ -603,6 +603,7 @@ def run_autograd(args, rank, world, local_rank):
             X = X if k == 1 else X.reshape(A.n, k)
             W = torch.rand((A.m,) if k == 1 else (A.m, k), dtype=dtype, device=dev)
             op.forward_raw(v, X)
+            op.tplan.prepare(dtype, k, tune=True)  # tuned dX plan (one-time, like the forward plan)
             for _ in range(args.warmup):
                 op.forward_raw(v, X)
                 op.tplan.backward(v, X, W)
@@ -622,7 +623,8 @@ def run_autograd(args, rank, world, local_rank):
             bw = statistics.mean(x.elapsed_time(y) for x, y in bwd)
             results.append({"dtype": str(dtype).replace("torch.", ""), "k": k, "fwd_ms": f, "bwd_ms": bw,
                             "bwd_over_fwd": bw / f, "fwd_gflops": 2.0 * A.nnz * k / (f * 1e-3) / 1e9,
-                            "bwd_gflops": 4.0 * A.nnz * k / (bw * 1e-3) / 1e9})
+                            "bwd_gflops": 4.0 * A.nnz * k / (bw * 1e-3) / 1e9,
+                            "fwd_config": op.plan(dtype, k).config, "dX_config": op.tplan.config(dtype, k)})
     main_r = results[0]
     line = {
         "metric": METRIC, "value": main_r["fwd_gflops"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

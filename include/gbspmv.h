@@ -246,8 +246,9 @@ int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx
  * row of A^T the entries keep their order of storage in A, so the result is
  * unique and bit-exact (no atomics decide any position).  The plan owns
  *   rowptrT[n+1], colT[nnz] (row of A of each entry), perm[nnz] (position in
- *   A of each entry of A^T), the row of every nonzero of A, and nnz doubles
- *   of scratch for the permuted values.
+ *   A of each entry of A^T) and the row of every nonzero of A (the dvals
+ *   pass); plus, only if a configuration that permutes the values first is
+ *   chosen, nnz doubles of scratch.
  * It does not keep row_ptr / col_idx.  Synchronises `stream`.
  * The transpose is the one-time set-up of the backward pass.
  */
@@ -264,9 +265,24 @@ int gbs_tplan_destroy(gbs_tplan* plan);
  * Make (and keep) a plan of A^T for `dtype` and k, with gbs_plan_create's
  * flags (GBS_PLAN_TUNE to autotune it); spmv_csr_backward then computes dX with
  * that plan's configuration instead of the one picked from A^T's row
- * statistics.  Synchronises `stream`.  Idempotent per (dtype, k).
+ * statistics.  dX reads A's values in place through perm (ROWS or
+ * MERGE_DIRECT); with GBS_PLAN_TUNE the tuner also times permuting the
+ * values into scratch first (one extra pass) followed by the best of all
+ * variants, and keeps that route if it is faster.  Synchronises `stream`.
+ * Idempotent per (dtype, k).
  */
 int gbs_tplan_prepare(gbs_tplan* plan, int dtype, int k, int flags, void* stream);
+/*
+ * Set the configuration of dX for (dtype, k), replacing a prepared one.
+ * GBS_VARIANT_ROWS and GBS_VARIANT_MERGE_DIRECT read A's values in place
+ * through perm; GBS_VARIANT_ROWS_TMA and GBS_VARIANT_MERGE permute them into
+ * plan-owned scratch first (allocated here, nnz doubles); GBS_VARIANT_AUTO
+ * takes the configuration from A^T's row statistics.  Errors as
+ * gbs_plan_set_config.  Synchronises `stream`.
+ */
+int gbs_tplan_set_config(gbs_tplan* plan, int dtype, int k, const gbs_config* cfg, void* stream);
+/* The configuration dX uses for (dtype, k): the prepared one, else the one from A^T's row statistics. */
+int gbs_tplan_get_config(const gbs_tplan* plan, int dtype, int k, gbs_config* cfg);
 
 /*
  * Backward of Y = A X (k >= 1 columns; k == 1 is SpMV) for a loss L with
@@ -274,9 +290,10 @@ int gbs_tplan_prepare(gbs_tplan* plan, int dtype, int k, int flags, void* stream
  *   dX[j, c] = sum_{p : col_idx[p] = j} vals[p] * dY[row(p), c]   i.e. dX = A^T dY
  *   dvals[p] = sum_c dY[row(p), c] * X[col_idx[p], c]             (sampled dense-dense product)
  * dX (n x k, ld lddx) and dvals (nnz) may each be NULL to skip that output.
- * dX runs the forward kernels on A^T (values permuted into the plan's
- * scratch, so calls that share a plan must be ordered on one stream); dvals
- * sums each nonzero's k products in column order.  `plan` must come from
+ * dX runs the forward kernels on A^T, reading A's values through perm (or,
+ * for a configuration that permutes them first, through the plan's scratch:
+ * calls that share such a plan must be ordered on one stream); dvals sums
+ * each nonzero's k products in column order.  `plan` must come from
  * gbs_transpose_plan on the same (row_ptr, col_idx); row_ptr is unused.
  */
 int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, const void* vals, int dtype,

@@ -264,6 +264,20 @@ class TransposePlan:
         _capi.check(lib().gbs_tplan_prepare(self._h, dt, int(k), _capi.PLAN_TUNE if tune else 0,
                                             _stream(self.device, stream)), "gbs_tplan_prepare")
 
+    def set_config(self, dtype, k: int, cfg, stream=None) -> None:
+        """Configuration of dX = A^T dY for dtype and k.  ROWS and MERGE_DIRECT read A's values in
+        place through the transpose permutation; ROWS_TMA and MERGE permute them first."""
+        dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
+        _capi.check(lib().gbs_tplan_set_config(self._h, dt, int(k), ctypes.byref(_config(cfg)),
+                                               _stream(self.device, stream)), "gbs_tplan_set_config")
+
+    def config(self, dtype, k: int) -> dict:
+        """The configuration dX uses for dtype and k (prepared, or picked from A^T's row statistics)."""
+        dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
+        c = gbs_config()
+        _capi.check(lib().gbs_tplan_get_config(self._h, dt, int(k), ctypes.byref(c)), "gbs_tplan_get_config")
+        return c.as_dict()
+
     def backward(self, vals, X, dY, need_dX: bool = True, need_dvals: bool = True, stream=None):
         """(dX, dvals) of Y = A X for upstream dY; X and dY are 1-D (SpMV) or 2-D row major."""
         _need_cuda(vals, X, dY)

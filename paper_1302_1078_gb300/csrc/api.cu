@@ -168,6 +168,9 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
   const int P = panel_cols(dtype, vec16);
   const size_t es = dsize(dtype);
   cudaError_t e = cudaSuccess;
+  const bool perm = A.perm != nullptr;
+  if (perm && cfg.variant != GBS_VARIANT_ROWS && cfg.variant != GBS_VARIANT_MERGE_DIRECT)
+    return fail(GBS_EUNSUPPORTED, "values read through a permutation need the ROWS or MERGE_DIRECT variant");
   if (cfg.variant == GBS_VARIANT_ROWS_TMA && status && aligned16(A.vals) && aligned16(A.col_idx)) {
     for (int c0 = 0; c0 < k; c0 += P) {
       const int kp = std::min(P, k - c0);
@@ -186,8 +189,9 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
       int lanes = cfg.lanes;
       if (k > 1) lanes = std::max(lanes, col_lanes(kp, dtype, vec16));
       DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
-      e = dtype == GBS_F64 ? launch_rows_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, A.m, s)
-                           : launch_rows_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, A.m, s);
+      auto launch = dtype == GBS_F64 ? (perm ? launch_rows_perm_f64 : launch_rows_f64)
+                                     : (perm ? launch_rows_perm_f32 : launch_rows_f32);
+      e = launch(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, A.m, s);
       if (e != cudaSuccess) return cuda_fail(e, "ROWS launch");
     }
     return GBS_OK;
@@ -216,8 +220,9 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
     const int kp = std::min(P, k - c0);
     DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
     const bool direct = cfg.variant == GBS_VARIANT_MERGE_DIRECT;
-    e = dtype == GBS_F64 ? launch_merge_f64(A, D, g, vec16, direct, cfg.threads, G.items, use->s, s)
-                         : launch_merge_f32(A, D, g, vec16, direct, cfg.threads, G.items, use->s, s);
+    auto launch = dtype == GBS_F64 ? (perm ? launch_merge_perm_f64 : launch_merge_f64)
+                                   : (perm ? launch_merge_perm_f32 : launch_merge_f32);
+    e = launch(A, D, g, vec16, direct, cfg.threads, G.items, use->s, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "MERGE launch");
   }
   if (use == &local) {
@@ -558,6 +563,8 @@ struct gbs_plan {
   bool coords_ready = false;
   int flags = 0;
   int* status = nullptr;  // device word: bounded-wait status of the pipelined variant
+  const int* perm = nullptr;  // values read through this permutation (plans of A^T inside a transpose plan)
+  float tuned_ms = 0.0f;      // the tuner's time of the chosen configuration (0: not tuned)
 };
 
 namespace {
@@ -605,7 +612,7 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
 }
 
 int plan_run(const gbs_plan* p, const void* vals, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t s) {
-  CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, vals};
+  CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, vals, p->perm};
   if (is_merge(p->cfg.variant)) {
     // the partition was made for 128-bit column access; if this call cannot use it the
     // lane count differs and the stream-ordered path is used instead
@@ -675,6 +682,13 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
     add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, 0);
   }
+  if (p->perm) {
+    // values through a permutation: the variants that support it
+    std::vector<gbs_config> keep;
+    for (const gbs_config& g : c)
+      if ((g.variant == GBS_VARIANT_ROWS || g.variant == GBS_VARIANT_MERGE_DIRECT) && g.emul == 0) keep.push_back(g);
+    c.swap(keep);
+  }
   return c;
 }
 
@@ -725,6 +739,7 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
       }
     }
     p->cfg = best_cfg;
+    p->tuned_ms = best < 1e30f ? best : 0.0f;
     rc = plan_prepare(p, s);
   }
   if (ev0) cudaEventDestroy(ev0);
@@ -736,12 +751,10 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
   return rc;
 }
 
-}  // namespace
-
-extern "C" {
-
-int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx, int dtype, int k,
-                    int flags, void* stream) {
+// gbs_plan_create with an optional permutation through which the values are read
+// (perm != nullptr: the plan is restricted to the ROWS and MERGE_DIRECT variants).
+int plan_create_impl(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx, int dtype, int k,
+                     int flags, const int* perm, void* stream) {
   if (plan == nullptr) return fail(GBS_EINVAL, "plan is NULL");
   *plan = nullptr;
   if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
@@ -763,6 +776,7 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   p->row_ptr = row_ptr;
   p->col_idx = col_idx;
   p->flags = flags;
+  p->perm = perm;
   cudaGetDevice(&p->device);
   if (cudaMalloc(reinterpret_cast<void**>(&p->status), 256) != cudaSuccess ||
       cudaMemsetAsync(p->status, 0, 256, s) != cudaSuccess) {
@@ -773,6 +787,7 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   rc = compute_stats(m, n, nnz, row_ptr, &p->stats, s);
   if (rc == GBS_OK) {
     p->cfg = heuristic_config(p->stats, dtype, k);
+    if (perm && p->cfg.variant == GBS_VARIANT_MERGE) p->cfg.variant = GBS_VARIANT_MERGE_DIRECT;
     rc = (flags & GBS_PLAN_TUNE) && m > 0 ? plan_tune(p, s) : plan_prepare(p, s);
   }
   if (rc != GBS_OK) {
@@ -783,6 +798,15 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
   }
   *plan = p;
   return GBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx, int dtype, int k,
+                    int flags, void* stream) {
+  return plan_create_impl(plan, m, n, nnz, row_ptr, col_idx, dtype, k, flags, nullptr, stream);
 }
 
 int gbs_plan_destroy(gbs_plan* plan) {
@@ -844,22 +868,65 @@ int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx
 
 struct gbs_tplan {
   int m = 0, n = 0, nnz = 0, device = 0;
-  int* rptrT = nullptr;  // n + 1
-  int* colT = nullptr;   // nnz
-  int* perm = nullptr;   // nnz
-  int* rows = nullptr;   // nnz: row of every nonzero of A
-  void* valsT = nullptr; // nnz doubles (scratch for the permuted values)
+  int* rptrT = nullptr;      // n + 1
+  int* colT = nullptr;       // nnz
+  int* perm = nullptr;       // nnz
+  int* rows = nullptr;       // nnz: row of every nonzero of A (the dvals pass)
   void* base = nullptr;
+  void* valsT = nullptr;     // nnz values, only for a prepared plan that permutes the values first
   gbs_stats statsT{};
   struct Prepared {
     int dtype, k;
-    gbs_plan* plan;
+    gbs_plan* plan;  // plan of A^T: reads A's values through perm, or valsT if `gather`
+    bool gather;
   };
-  std::vector<Prepared> plans;  // plans of A^T, one per (dtype, k), made by gbs_tplan_prepare
+  std::vector<Prepared> plans;  // one per (dtype, k), made by gbs_tplan_prepare
 };
 
 namespace {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Time `fn` (enqueued on s) as the median of 3 runs after one warm-up; returns ms or -1.
+template <typename F>
+float time_median(F fn, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return -1.0f;
+  }
+  float t[3] = {0, 0, 0};
+  bool ok = true;
+  for (int r = 0; r < 4 && ok; ++r) {
+    ok = cudaEventRecord(e0, s) == cudaSuccess && fn() && cudaEventRecord(e1, s) == cudaSuccess &&
+         cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0;
+    if (ok) cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) t[r - 1] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return -1.0f;
+  std::sort(t, t + 3);
+  return t[1];
+}
+
+// Keep `plan` as the prepared plan of A^T for (dtype, k), replacing an earlier one.
+int tplan_install(gbs_tplan* t, int dtype, int k, gbs_plan* plan, bool gather) {
+  if (gather && !t->valsT && cudaMalloc(&t->valsT, (size_t)std::max(t->nnz, 1) * 8) != cudaSuccess) {
+    t->valsT = nullptr;
+    gbs_plan_destroy(plan);
+    return fail(GBS_ENOMEM, "cudaMalloc (permuted values)");
+  }
+  for (auto& pp : t->plans)
+    if (pp.dtype == dtype && pp.k == k) {
+      gbs_plan_destroy(pp.plan);
+      pp.plan = plan;
+      pp.gather = gather;
+      return GBS_OK;
+    }
+  t->plans.push_back({dtype, k, plan, gather});
+  return GBS_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -881,8 +948,8 @@ int gbs_transpose_plan(gbs_tplan** out, int m, int n, int nnz, const int* row_pt
   t->nnz = nnz;
   cudaGetDevice(&t->device);
   const size_t z = (size_t)std::max(nnz, 1);
-  size_t b_rptr = align256(sizeof(int) * ((size_t)n + 1)), b_i = align256(sizeof(int) * z), b_v = align256(8 * z);
-  size_t keep = b_rptr + 3 * b_i + b_v;
+  size_t b_rptr = align256(sizeof(int) * ((size_t)n + 1)), b_i = align256(sizeof(int) * z);
+  size_t keep = b_rptr + 3 * b_i;
   size_t b_hist = align256(sizeof(int) * transpose_hist_ints(nnz));
   size_t b_scan = align256(sizeof(int) * transpose_scan_ws_ints(nnz));
   size_t tmp = 4 * b_i + b_hist + b_scan;
@@ -899,8 +966,6 @@ int gbs_transpose_plan(gbs_tplan** out, int m, int n, int nnz, const int* row_pt
   t->perm = reinterpret_cast<int*>(p);
   p += b_i;
   t->rows = reinterpret_cast<int*>(p);
-  p += b_i;
-  t->valsT = p;
   void* work = nullptr;
   e = cudaMallocAsync(&work, tmp, s);
   if (e == cudaSuccess) {
@@ -954,6 +1019,7 @@ int gbs_tplan_export(const gbs_tplan* t, int* rowptrT, int* colT, int* perm, voi
 int gbs_tplan_destroy(gbs_tplan* t) {
   if (!t) return GBS_OK;
   for (auto& pp : t->plans) gbs_plan_destroy(pp.plan);
+  if (t->valsT) cudaFree(t->valsT);
   if (t->base) cudaFree(t->base);
   delete t;
   return GBS_OK;
@@ -965,10 +1031,68 @@ int gbs_tplan_prepare(gbs_tplan* t, int dtype, int k, int flags, void* stream) {
   if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
   for (auto& pp : t->plans)
     if (pp.dtype == dtype && pp.k == k) return GBS_OK;
-  gbs_plan* p = nullptr;
-  int rc = gbs_plan_create(&p, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, flags & ~GBS_PLAN_CHECK, stream);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  flags &= ~GBS_PLAN_CHECK;
+  gbs_plan* pp = nullptr;  // A^T reading A's values through perm
+  int rc = plan_create_impl(&pp, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, flags, t->perm, stream);
   if (rc) return rc;
-  t->plans.push_back({dtype, k, p});
+  bool gather = false;
+  gbs_plan* pg = nullptr;  // A^T on values permuted by a separate gather
+  if ((flags & GBS_PLAN_TUNE) && t->nnz > 0 && pp->tuned_ms > 0) {
+    // the alternative route: permute the values once per call, then the best plain plan of A^T
+    rc = plan_create_impl(&pg, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, flags, nullptr, stream);
+    if (rc == GBS_OK && pg->tuned_ms > 0 && pg->tuned_ms < pp->tuned_ms) {
+      void *src = nullptr, *dst = nullptr;
+      const size_t bytes = (size_t)t->nnz * dsize(dtype);
+      float tg = -1.0f;
+      if (cudaMalloc(&src, bytes) == cudaSuccess && cudaMalloc(&dst, bytes) == cudaSuccess &&
+          cudaMemsetAsync(src, 0, bytes, s) == cudaSuccess)
+        tg = time_median([&] { return gather_values(dtype, src, t->perm, t->nnz, dst, s) == cudaSuccess; }, s);
+      if (src) cudaFree(src);
+      if (dst) cudaFree(dst);
+      gather = tg >= 0 && tg + pg->tuned_ms < pp->tuned_ms;
+    }
+    if (tune_log())
+      std::fprintf(stderr, "gbspmv tplan prepare k=%d: through perm %.4f ms, gather + plain %s\n", k, pp->tuned_ms,
+                   gather ? "chosen" : "not chosen");
+    g_err.clear();
+    rc = GBS_OK;
+  }
+  if (gather) {
+    gbs_plan_destroy(pp);
+    return tplan_install(t, dtype, k, pg, true);
+  }
+  if (pg) gbs_plan_destroy(pg);
+  return tplan_install(t, dtype, k, pp, false);
+}
+
+int gbs_tplan_set_config(gbs_tplan* t, int dtype, int k, const gbs_config* cfg, void* stream) {
+  if (!t || !cfg) return fail(GBS_EINVAL, "NULL pointer");
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  const bool gather = cfg->variant == GBS_VARIANT_ROWS_TMA || cfg->variant == GBS_VARIANT_MERGE;
+  gbs_plan* p = nullptr;
+  int rc = plan_create_impl(&p, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, 0, gather ? nullptr : t->perm,
+                            stream);
+  if (rc) return rc;
+  if (cfg->variant != GBS_VARIANT_AUTO) {
+    rc = gbs_plan_set_config(p, cfg);
+    if (rc) {
+      gbs_plan_destroy(p);
+      return rc;
+    }
+  }
+  return tplan_install(t, dtype, k, p, gather);
+}
+
+int gbs_tplan_get_config(const gbs_tplan* t, int dtype, int k, gbs_config* cfg) {
+  if (!t || !cfg) return fail(GBS_EINVAL, "NULL pointer");
+  for (auto& pp : t->plans)
+    if (pp.dtype == dtype && pp.k == k) return gbs_plan_get_config(pp.plan, cfg);
+  if (!valid_dtype(dtype) || k < 1) return fail(GBS_EINVAL, "dtype or k");
+  gbs_config c = heuristic_config(t->statsT, dtype, k);
+  if (c.variant == GBS_VARIANT_MERGE) c.variant = GBS_VARIANT_MERGE_DIRECT;
+  *cfg = c;
   return GBS_OK;
 }
 
@@ -985,18 +1109,22 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (dX) {
-    // dX = A^T dY through the precomputed transpose: values permuted once per call
-    e = gather_values(dtype, vals, t->perm, t->nnz, t->valsT, s);
-    if (e != cudaSuccess) return cuda_fail(e, "gather of A^T values");
-    const gbs_plan* prepared = nullptr;
+    // dX = A^T dY on the precomputed transpose
+    const gbs_tplan::Prepared* prepared = nullptr;
     for (auto& pp : t->plans)
-      if (pp.dtype == dtype && pp.k == k) prepared = pp.plan;
+      if (pp.dtype == dtype && pp.k == k) prepared = &pp;
     int rc;
-    if (prepared) {
-      rc = plan_run(prepared, t->valsT, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, s);
+    if (prepared && prepared->gather) {
+      e = gather_values(dtype, vals, t->perm, t->nnz, t->valsT, s);
+      if (e != cudaSuccess) return cuda_fail(e, "gather of A^T values");
+      rc = plan_run(prepared->plan, t->valsT, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, s);
+    } else if (prepared) {
+      rc = plan_run(prepared->plan, vals, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, s);
     } else {
-      CsrView AT{t->n, t->m, t->nnz, t->rptrT, t->colT, t->valsT};
+      // A's values read in place through perm, configuration from A^T's row statistics
+      CsrView AT{t->n, t->m, t->nnz, t->rptrT, t->colT, vals, t->perm};
       gbs_config c = heuristic_config(t->statsT, dtype, k);
+      if (c.variant == GBS_VARIANT_MERGE) c.variant = GBS_VARIANT_MERGE_DIRECT;
       rc = run_product(AT, dtype, k, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, c, nullptr, false, s);
     }
     if (rc) return rc;

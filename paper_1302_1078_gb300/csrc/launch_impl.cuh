@@ -16,25 +16,26 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT>
+template <typename T, int VEC, int LANES, bool SPLIT, bool PERM>
 static cudaError_t rows_go(const RowsArgs<T>& a, int grid, int threads, size_t smem, cudaStream_t s) {
-  auto kern = rows_kernel<T, VEC, LANES, SPLIT>;
+  auto kern = rows_kernel<T, VEC, LANES, SPLIT, PERM>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int LANES>
+template <typename T, int LANES, bool PERM>
 static cudaError_t rows_lanes(const RowsArgs<T>& a, bool split, bool vec16, int grid, int threads, size_t smem,
                               cudaStream_t s) {
   constexpr int V = 16 / (int)sizeof(T);
-  if (split) return rows_go<T, 1, LANES, true>(a, grid, threads, smem, s);
-  if (vec16) return rows_go<T, V, LANES, false>(a, grid, threads, smem, s);
-  return rows_go<T, 1, LANES, false>(a, grid, threads, smem, s);
+  if (split) return rows_go<T, 1, LANES, true, PERM>(a, grid, threads, smem, s);
+  if (vec16) return rows_go<T, V, LANES, false, PERM>(a, grid, threads, smem, s);
+  return rows_go<T, 1, LANES, false, PERM>(a, grid, threads, smem, s);
 }
 
-template <typename T>
+// PERM: A.perm is set and the value of entry p is A.vals[A.perm[p]].
+template <typename T, bool PERM = false>
 cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
                           int row_base, int rows, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
@@ -50,19 +51,20 @@ cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool 
   a.ldy = D.ldy;
   a.tile = tile;
   a.row_base = row_base;
-  a.aligned_vals = (reinterpret_cast<uintptr_t>(A.vals) & 15) == 0;
+  a.perm = PERM ? A.perm : nullptr;
+  a.aligned_vals = (reinterpret_cast<uintptr_t>(PERM ? static_cast<const void*>(A.perm) : A.vals) & 15) == 0;
   a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
   const int rpc = threads / lanes;
   const int grid = (rows + rpc - 1) / rpc;
   const size_t smem = rows_smem_bytes<T>(rpc, tile);
   const bool split = D.k == 1;
   switch (lanes) {
-    case 1: return rows_lanes<T, 1>(a, split, vec16, grid, threads, smem, s);
-    case 2: return rows_lanes<T, 2>(a, split, vec16, grid, threads, smem, s);
-    case 4: return rows_lanes<T, 4>(a, split, vec16, grid, threads, smem, s);
-    case 8: return rows_lanes<T, 8>(a, split, vec16, grid, threads, smem, s);
-    case 16: return rows_lanes<T, 16>(a, split, vec16, grid, threads, smem, s);
-    case 32: return rows_lanes<T, 32>(a, split, vec16, grid, threads, smem, s);
+    case 1: return rows_lanes<T, 1, PERM>(a, split, vec16, grid, threads, smem, s);
+    case 2: return rows_lanes<T, 2, PERM>(a, split, vec16, grid, threads, smem, s);
+    case 4: return rows_lanes<T, 4, PERM>(a, split, vec16, grid, threads, smem, s);
+    case 8: return rows_lanes<T, 8, PERM>(a, split, vec16, grid, threads, smem, s);
+    case 16: return rows_lanes<T, 16, PERM>(a, split, vec16, grid, threads, smem, s);
+    case 32: return rows_lanes<T, 32, PERM>(a, split, vec16, grid, threads, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -139,9 +141,9 @@ cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, b
   }
 }
 
-template <typename T, int VEC, int G, bool DIRECT>
+template <typename T, int VEC, int G, bool DIRECT, bool PERM>
 static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
-  auto kern = merge_kernel<T, VEC, G, DIRECT>;
+  auto kern = merge_kernel<T, VEC, G, DIRECT, PERM>;
   const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -152,18 +154,23 @@ static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-template <typename T, int G>
+template <typename T, int G, bool PERM>
 static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, bool direct, int threads, cudaStream_t s) {
   constexpr int V = 16 / (int)sizeof(T);
   if (direct) {
-    if (vec16 && a.k > 1) return merge_go<T, V, G, true>(a, threads, s);
-    return merge_go<T, 1, G, true>(a, threads, s);
+    if (vec16 && a.k > 1) return merge_go<T, V, G, true, PERM>(a, threads, s);
+    return merge_go<T, 1, G, true, PERM>(a, threads, s);
   }
-  if (vec16 && a.k > 1) return merge_go<T, V, G, false>(a, threads, s);
-  return merge_go<T, 1, G, false>(a, threads, s);
+  if constexpr (PERM) {
+    return cudaErrorInvalidValue;  // permuted values: direct form only
+  } else {
+    if (vec16 && a.k > 1) return merge_go<T, V, G, false, false>(a, threads, s);
+    return merge_go<T, 1, G, false, false>(a, threads, s);
+  }
 }
 
-template <typename T>
+// PERM: A.perm is set and the value of entry p is A.vals[A.perm[p]] (direct form only).
+template <typename T, bool PERM = false>
 cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
                            int items, const MergeScratch& S, cudaStream_t s) {
   if (A.m == 0) return cudaSuccess;
@@ -183,15 +190,16 @@ cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec
   a.coords = S.coords;
   a.carry_row = S.carry_row;
   a.carry_val = static_cast<T*>(S.carry_val);
-  a.aligned_vals = (reinterpret_cast<uintptr_t>(A.vals) & 15) == 0;
+  a.perm = PERM ? A.perm : nullptr;
+  a.aligned_vals = (reinterpret_cast<uintptr_t>(PERM ? static_cast<const void*>(A.perm) : A.vals) & 15) == 0;
   a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
   switch (g) {
-    case 1: return merge_g<T, 1>(a, vec16, direct, threads, s);
-    case 2: return merge_g<T, 2>(a, vec16, direct, threads, s);
-    case 4: return merge_g<T, 4>(a, vec16, direct, threads, s);
-    case 8: return merge_g<T, 8>(a, vec16, direct, threads, s);
-    case 16: return merge_g<T, 16>(a, vec16, direct, threads, s);
-    case 32: return merge_g<T, 32>(a, vec16, direct, threads, s);
+    case 1: return merge_g<T, 1, PERM>(a, vec16, direct, threads, s);
+    case 2: return merge_g<T, 2, PERM>(a, vec16, direct, threads, s);
+    case 4: return merge_g<T, 4, PERM>(a, vec16, direct, threads, s);
+    case 8: return merge_g<T, 8, PERM>(a, vec16, direct, threads, s);
+    case 16: return merge_g<T, 16, PERM>(a, vec16, direct, threads, s);
+    case 32: return merge_g<T, 32, PERM>(a, vec16, direct, threads, s);
     default: return cudaErrorInvalidValue;
   }
 }

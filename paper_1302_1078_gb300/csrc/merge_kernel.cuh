@@ -33,6 +33,8 @@
 //     direct form needs only the row-pointer window in shared memory (4 bytes
 //     per item instead of 16), which allows more items per thread at the same
 //     residency and spreads the carry scan over more nonzeros.
+//   * PERM (direct form only): the value of stored entry p is vals[perm[p]],
+//     so the backward pass can run A^T on A's values without a permuted copy.
 #pragma once
 #include "device_common.cuh"
 
@@ -52,7 +54,8 @@ struct MergeArgs {
   const int2* __restrict__ coords;  // [ctas + 1] (row, nonzero) at the start of each tile
   int* __restrict__ carry_row;      // [ctas]
   T* __restrict__ carry_val;        // [ctas * k]
-  bool aligned_vals, aligned_cols;
+  bool aligned_vals, aligned_cols;  // aligned_vals: perm when PERM
+  const int* __restrict__ perm = nullptr;  // PERM: value of entry p is vals[perm[p]]
 };
 
 // Merge-path search: split diagonal d of the (row ends x nonzeros) grid.
@@ -86,8 +89,9 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
 
 // One merge-path tile b of the product (the whole CTA works on it).  Used by the
 // standalone kernel below and by the batched persistent kernel.
-template <typename T, int VEC, int G, bool DIRECT = false>
+template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false>
 __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
+  static_assert(!PERM || DIRECT, "permuted values need the direct form");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = blockDim.x / G;
   const int nw = blockDim.x / 32;
@@ -198,7 +202,11 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       return xv;
     };
     auto one = [&](int q) {
-      const T vv = ld_stream(a.vals + q, pol_stream);
+      T vv;
+      if constexpr (PERM)
+        vv = __ldg(a.vals + ld_stream(a.perm + q, pol_stream));
+      else
+        vv = ld_stream(a.vals + q, pol_stream);
       const int cc = ld_stream(a.col_idx + q, pol_stream);
       Vec<T, VEC> xv;
       if (col_active) xv = gather(cc);
@@ -216,7 +224,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       for (; nz < nz_e && (nz & 3); ++nz) one(nz);
       for (; nz + 4 <= nz_e; nz += 4) {
         T v[4];
-        if constexpr (sizeof(T) == 8) {
+        if constexpr (PERM) {
+          const uint4 pw = ld_stream_l1_v4(a.perm + nz, pol_stream);
+          v[0] = __ldg(a.vals + (int)pw.x);
+          v[1] = __ldg(a.vals + (int)pw.y);
+          v[2] = __ldg(a.vals + (int)pw.z);
+          v[3] = __ldg(a.vals + (int)pw.w);
+        } else if constexpr (sizeof(T) == 8) {
           const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
           const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
           v[0] = __hiloint2double((int)w0.y, (int)w0.x);
@@ -376,9 +390,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   }
 }
 
-template <typename T, int VEC, int G, bool DIRECT>
+template <typename T, int VEC, int G, bool DIRECT, bool PERM = false>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
-  merge_tile<T, VEC, G, DIRECT>(a, blockIdx.x);
+  merge_tile<T, VEC, G, DIRECT, PERM>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of

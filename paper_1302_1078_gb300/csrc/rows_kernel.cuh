@@ -19,6 +19,10 @@
 //
 // Summation order per output element is fixed (each lane in stored order,
 // then a fixed shuffle tree), so results are bitwise reproducible.
+//
+// PERM: the value of stored entry p is vals[perm[p]] (the backward pass runs
+// A^T with A's values in place, perm being the transpose permutation).  The
+// CTA then stages perm instead of vals and gathers each value once.
 #pragma once
 #include "device_common.cuh"
 
@@ -35,8 +39,9 @@ struct RowsArgs {
   long long ldx, ldy;
   int tile;            // nonzeros staged per pass
   int row_base;        // first row of block 0 (for batched / split launches)
-  bool aligned_vals;   // vals 16-byte aligned
+  bool aligned_vals;   // vals (perm when PERM) 16-byte aligned
   bool aligned_cols;   // col_idx 16-byte aligned
+  const int* __restrict__ perm = nullptr;  // PERM: value of entry p is vals[perm[p]]
 };
 
 // Shared-memory layout: s_rp[rows + 1] | s_val[tile + 4] | s_col[tile + 4]
@@ -50,7 +55,7 @@ __host__ __device__ inline size_t rows_smem_bytes(int rows_per_cta, int tile) {
 
 constexpr int kUnroll = 4;
 
-template <typename T, int VEC, int LANES, bool SPLIT>
+template <typename T, int VEC, int LANES, bool SPLIT, bool PERM = false>
 __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rpc = blockDim.x / LANES;
@@ -81,11 +86,21 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
   const bool col_full = SPLIT ? true : (c_lo + VEC <= a.k);
 
   Acc<T> acc[VEC];
+  // value of the staged entry at offset i of the tile
+  auto val_at = [&](int i) -> T {
+    if constexpr (PERM)
+      return __ldg(a.vals + reinterpret_cast<const int*>(s_val)[i]);
+    else
+      return s_val[i];
+  };
 
   for (int c0 = bs; c0 < be; c0 += tile) {
     const int c1 = min(be, c0 + tile);
     const int a0 = c0 & ~3;
-    stage_copy<T>(s_val, a.vals, a0, c1, a.aligned_vals, pol_stream);
+    if constexpr (PERM)
+      stage_copy<int>(reinterpret_cast<int*>(s_val), a.perm, a0, c1, a.aligned_vals, pol_stream);
+    else
+      stage_copy<T>(s_val, a.vals, a0, c1, a.aligned_vals, pol_stream);
     stage_copy<int>(s_col, a.col_idx, a0, c1, a.aligned_cols, pol_stream);
     __syncthreads();
     if (active && col_active) {
@@ -104,7 +119,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
           int c[kUnroll];
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
-            v[u] = s_val[p + u * STEP - a0];
+            v[u] = val_at(p + u * STEP - a0);
             c[u] = s_col[p + u * STEP - a0];
           }
           Vec<T, VEC> xv[kUnroll];
@@ -116,7 +131,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
             for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
         }
         for (; p < hi; p += STEP) {
-          const T v = s_val[p - a0];
+          const T v = val_at(p - a0);
           const int c = s_col[p - a0];
           Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
 #pragma unroll
@@ -126,7 +141,7 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
         // ragged last column slice: scalar gathers of the valid columns
         const int nv = a.k - c_lo;
         for (; p < hi; p += STEP) {
-          const T v = s_val[p - a0];
+          const T v = val_at(p - a0);
           const T* xr = Xc + (long long)s_col[p - a0] * a.ldx;
 #pragma unroll
           for (int j = 0; j < VEC; ++j)
@@ -158,9 +173,9 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
   }
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT>
+template <typename T, int VEC, int LANES, bool SPLIT, bool PERM = false>
 __global__ void __launch_bounds__(1024) rows_kernel(RowsArgs<T> a) {
-  rows_block<T, VEC, LANES, SPLIT>(a, blockIdx.x);
+  rows_block<T, VEC, LANES, SPLIT, PERM>(a, blockIdx.x);
 }
 
 }  // namespace gbs

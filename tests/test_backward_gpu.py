@@ -85,6 +85,100 @@ def test_backward_matches_oracle(gbs, name, k, dtype):
     assert torch.equal(dX, dX2) and torch.equal(dvals, dvals2)
 
 
+def rows_chunk_edges():
+    """Row lengths that put row boundaries, empty rows and long rows across the 128-nonzero chunks
+    the dvals pass uses to find each nonzero's row."""
+    rng = np.random.default_rng(41)
+    lens = [0] * 300 + [1000] + [0] * 300 + [1] * 257 + [129, 127, 128, 0, 0, 255, 1] + [0] * 50 + [3] * 40 + [0]
+    lens = np.array(lens, dtype=np.int64)
+    rp = np.zeros(lens.size + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(lens)
+    n = 1200
+    ci = np.concatenate([np.sort(rng.choice(n, size=l, replace=False)) for l in lens]).astype(np.int32)
+    return synth.CSR(lens.size, n, rp, ci, synth.normal(int(rp[-1]), seed=42))
+
+
+CASES["chunk_edges"] = rows_chunk_edges
+
+V = {"ROWS": 1, "MERGE": 2, "ROWS_TMA": 3, "MERGE_DIRECT": 4}
+AT_CONFIGS = [
+    # values read in place through the transpose permutation
+    dict(variant=V["ROWS"], lanes=1, threads=256, tile_nnz=2048),
+    dict(variant=V["ROWS"], lanes=2, threads=128, tile_nnz=64),
+    dict(variant=V["ROWS"], lanes=8, threads=256, tile_nnz=512),
+    dict(variant=V["ROWS"], lanes=32, threads=64, tile_nnz=96),
+    dict(variant=V["MERGE_DIRECT"], threads=256, items=31),
+    dict(variant=V["MERGE_DIRECT"], threads=64, items=7),
+    dict(variant=V["MERGE_DIRECT"], threads=128, items=63),
+    # values permuted into scratch first
+    dict(variant=V["ROWS_TMA"], lanes=2, threads=64),
+    dict(variant=V["MERGE"], threads=256, items=11),
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 8])
+@pytest.mark.parametrize("ci", range(len(AT_CONFIGS)))
+@pytest.mark.parametrize("name", ["random_rect", "dup_unsorted", "stencil2d_37", "rmat_14", "chunk_edges", "empty"])
+def test_backward_dX_configs(gbs, name, ci, k, dtype):
+    """Every dX route (values through perm, or permuted first) on every variant against the oracle."""
+    A = case(name)
+    cfg = AT_CONFIGS[ci]
+    v = A.vals.astype(NP[dtype])
+    X = synth.uniform(A.n * k, seed=13, stream=k).reshape(A.n, k).astype(NP[dtype])
+    W = synth.uniform(A.m * k, seed=14, stream=k).reshape(A.m, k).astype(NP[dtype])
+    dX_ref, dv_ref, RdX, Rdv = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, v, X, W)
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    try:
+        t.set_config(dtype, k, cfg)
+    except gbs._capi.GbsError as e:
+        # ROWS_TMA stages a whole row block: A^T of a power-law matrix can exceed it
+        if e.status == gbs._capi.GBS_EUNSUPPORTED and cfg["variant"] == V["ROWS_TMA"]:
+            pytest.skip(str(e))
+        raise
+    got = t.config(dtype, k)
+    assert got["variant"] == cfg["variant"]
+    Xa, Wa = (dev(X[:, 0]), dev(W[:, 0])) if k == 1 else (dev(X), dev(W))
+    dX, dvals = t.backward(dev(v), Xa, Wa)
+    within(dX, dX_ref, RdX, dtype, f"dX {name} k={k} {cfg}")
+    within(dvals, dv_ref, Rdv, dtype, f"dvals {name} k={k}")
+    dX2, _ = t.backward(dev(v), Xa, Wa, need_dvals=False)
+    assert torch.equal(dX, dX2)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 8])
+@pytest.mark.parametrize("name", ["banded_20k", "rmat_14", "chunk_edges"])
+def test_backward_prepared_tuned(gbs, name, k, dtype):
+    """dX through a tuned plan of A^T (either route) against the oracle; idempotent prepare."""
+    A = case(name)
+    v = A.vals.astype(NP[dtype])
+    X = synth.uniform(A.n * k, seed=15, stream=k).reshape(A.n, k).astype(NP[dtype])
+    W = synth.uniform(A.m * k, seed=16, stream=k).reshape(A.m, k).astype(NP[dtype])
+    dX_ref, _, RdX, _ = oracle.backward(A.m, A.n, A.row_ptr, A.col_idx, v, X, W)
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    t.prepare(dtype, k, tune=True)
+    cfg = t.config(dtype, k)
+    t.prepare(dtype, k, tune=True)
+    assert t.config(dtype, k) == cfg
+    Xa, Wa = (dev(X[:, 0]), dev(W[:, 0])) if k == 1 else (dev(X), dev(W))
+    dX, dvals = t.backward(dev(v), Xa, Wa, need_dvals=False)
+    assert dvals is None
+    within(dX, dX_ref, RdX, dtype, f"dX {name} k={k} tuned {cfg}")
+
+
+def test_backward_config_errors(gbs):
+    A = case("random_rect")
+    t = gbs.TransposePlan(dev(A.row_ptr), dev(A.col_idx), A.n)
+    with pytest.raises(Exception):
+        t.set_config(torch.float64, 1, dict(variant=V["ROWS"], lanes=3))
+    with pytest.raises(Exception):
+        t.set_config(torch.float64, 0, dict(variant=V["ROWS"]))
+    # AUTO: the statistics-based configuration, values in place
+    t.set_config(torch.float64, 1, dict(variant=0))
+    assert t.config(torch.float64, 1)["variant"] in (V["ROWS"], V["MERGE_DIRECT"])
+
+
 def test_autograd_gradcheck(gbs):
     A = synth.random_csr(12, 9, 0.3, 21, empty_rows=0.2)
     op = gbs.CsrOperator(dev(A.row_ptr), dev(A.col_idx), A.n)
