@@ -310,13 +310,16 @@ int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, c
  *     candidates with standalone launches on the given operands (this
  *     writes Y_b);
  *   - builds the work list: matrix b owns the contiguous items
- *     [item_begin[b], item_begin[b+1]) (row blocks or merge tiles), and
- *     item i is processed by CTA i mod grid, grid = every resident CTA slot;
+ *     [item_begin[b], item_begin[b+1]) (row blocks or merge tiles); the
+ *     grid is every resident CTA slot (`grid`), and each CTA claims the next
+ *     unclaimed item from a device counter that the graph zeroes before the
+ *     kernel, so launches of one plan must be ordered on one stream;
  *   - owns a device descriptor table, the merge scratch and the graph.
  * The arrays of every item must stay valid and unchanged while the plan is
  * used (only X and Y may be replaced, below).  Results equal
  * spmv_csr_batched_looped (one standalone launch per matrix with the same
- * configuration) bitwise.  Plan creation synchronises `stream`.
+ * configuration) bitwise, whichever CTA runs an item.  Plan creation
+ * synchronises `stream`.
  * k must fit one column panel (k <= 64 for FP64 / 128 for FP32 with 16-byte
  * aligned X/Y rows, else k <= 32).
  */

@@ -1151,6 +1151,7 @@ struct gbs_batch_plan {
   std::vector<unsigned char> h_desc;
   void* d_desc = nullptr;
   void* scratch = nullptr;
+  int* next_item = nullptr;  // device work counter, reset by the graph before every launch
   size_t smem = 0;
   int grid = 0, total_items = 0;
   cudaGraph_t graph = nullptr;
@@ -1160,6 +1161,9 @@ struct gbs_batch_plan {
 namespace {
 
 constexpr int kBatchThreads = 256;
+// Shared memory per CTA of the batched kernel: four 256-thread CTAs per SM (the kernel is
+// compiled for four) fit in 228 KB with 1 KB reserved per CTA.
+constexpr size_t kBatchSmemBudget = 54 * 1024;
 
 size_t rows_smem_host(int dtype, int rpc, int tile) {
   return dtype == GBS_F64 ? rows_smem_bytes<double>(rpc, tile) : rows_smem_bytes<float>(rpc, tile);
@@ -1212,6 +1216,7 @@ void batch_free(gbs_batch_plan* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->d_desc) cudaFree(p->d_desc);
   if (p->scratch) cudaFree(p->scratch);
+  if (p->next_item) cudaFree(p->next_item);
   delete p;
 }
 
@@ -1236,8 +1241,17 @@ std::vector<gbs_config> batch_candidates(const gbs_stats& st, int dtype, int k) 
     add(GBS_VARIANT_ROWS, 0, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile / 2, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 0);
+    add(GBS_VARIANT_MERGE, 0, 0, 15);
   }
   return c;
+}
+
+// Largest odd merge items per thread (at most `items`, at least 3) whose shared memory fits
+// the batched kernel's budget.
+int batch_cap_items(int dtype, int g, bool vec16, int items) {
+  int it = std::max(3, items | 1);
+  while (it > 3 && merge_smem_host(dtype, g, vec16, it, false) > kBatchSmemBudget) it -= 2;
+  return it;
 }
 
 }  // namespace
@@ -1305,6 +1319,11 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       float best = 1e30f;
       for (gbs_config cand : batch_candidates(st, dtype, k)) {
         if (k > 1 && cand.variant == GBS_VARIANT_ROWS) cand.lanes = p->G;
+        if (is_merge(cand.variant)) {
+          // time the tile size the batch will run (capped to the shared-memory budget)
+          const MergeGeom G = merge_geom(cand, it.m, it.nnz, dtype, k, vec16);
+          cand.items = batch_cap_items(dtype, G.g, vec16, G.items);
+        }
         CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
         float ms_sum = 0;
         bool ok = true;
@@ -1345,7 +1364,12 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       nitems = (it.m + rpc - 1) / rpc;
       p->smem = std::max(p->smem, rows_smem_host(dtype, rpc, c.tile_nnz));
     } else {
-      const MergeGeom G = merge_geom(c, it.m, it.nnz, dtype, k, vec16);
+      MergeGeom G = merge_geom(c, it.m, it.nnz, dtype, k, vec16);
+      const int capped = batch_cap_items(dtype, G.g, vec16, G.items);
+      if (capped != G.items) {
+        p->cfgs[b].items = capped;
+        G = merge_geom(p->cfgs[b], it.m, it.nnz, dtype, k, vec16);
+      }
       p->cfgs[b].items = G.items;
       nitems = it.m > 0 ? G.ctas : 0;
       p->smem = std::max(p->smem, merge_smem_host(dtype, G.g, vec16, G.items, c.variant == GBS_VARIANT_MERGE_DIRECT));
@@ -1387,11 +1411,13 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       fill_desc<float>(p, b, reinterpret_cast<BatchDesc<float>*>(p->h_desc.data() + dsz * b));
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, p->h_desc.size());
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->next_item), 256);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_desc, p->h_desc.data(), p->h_desc.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   // ---- persistent grid: every resident CTA slot of the GPU
   int bps = 0, sms = 0;
-  if (e == cudaSuccess) e = batched_kernel_call(false, dtype, p->split, p->G, vec16, nullptr, 0, 0, 0, p->smem, &bps, s);
+  if (e == cudaSuccess)
+    e = batched_kernel_call(false, dtype, p->split, p->G, vec16, nullptr, 0, 0, nullptr, 0, p->smem, &bps, s);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) {
     batch_free(p);
@@ -1404,8 +1430,11 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t el = batched_kernel_call(true, dtype, p->split, p->G, vec16, p->d_desc, nmat, p->total_items, p->grid,
-                                           p->smem, nullptr, cs);
+      // the work counter is zeroed by the graph itself, so every replay starts a fresh list
+      cudaError_t el = cudaMemsetAsync(p->next_item, 0, sizeof(int), cs);
+      if (el == cudaSuccess)
+        el = batched_kernel_call(true, dtype, p->split, p->G, vec16, p->d_desc, nmat, p->total_items, p->next_item,
+                                 p->grid, p->smem, nullptr, cs);
       e = cudaStreamEndCapture(cs, &p->graph);
       if (el != cudaSuccess) e = el;
     }

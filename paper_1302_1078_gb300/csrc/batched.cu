@@ -3,11 +3,15 @@
 // The paper multiplies one matrix at a time (Sec. 4, Sec. 5).  Serving many
 // small and uneven matrices one launch each leaves most of GB300's 152 SMs idle
 // for the small ones and pays a launch per matrix.  Here one persistent kernel
-// walks a work list of (matrix, row block | merge tile) items: item i is taken
-// by CTA i mod gridDim.x, the matrix comes from a binary search of the
-// descriptors' first items, and each item runs exactly the device function the
-// standalone kernels run (rows_block / merge_tile) with the matrix's own tuned
-// configuration, so the batched result equals the per-matrix loop bitwise.
+// walks a work list of (matrix, row block | merge tile) items.  A CTA takes the
+// next unclaimed item from a device counter (reset by the graph before every
+// launch), so the SMs stay busy until the list is exhausted whatever the items'
+// costs; the matrix comes from a binary search of the descriptors' first items
+// (a CTA's items only increase, so the search starts at its previous matrix),
+// and each item runs exactly the device function the standalone kernels run
+// (rows_block / merge_tile) with the matrix's own tuned configuration, so the
+// batched result equals the per-matrix loop bitwise: which CTA runs an item
+// does not change what the item computes.
 //
 // A merge-path matrix needs its per-tile carries added after all its tiles are
 // done.  The CTA that finishes a matrix's last tile (a per-matrix counter,
@@ -67,11 +71,16 @@ __device__ __forceinline__ MergeArgs<T> merge_args(const BatchDesc<T>& d) {
 
 // SPLIT (k == 1): ROWS lanes vary per matrix.  !SPLIT (k > 1): every matrix uses G column lanes.
 template <typename T, int VEC, bool SPLIT, int G>
-__global__ void __launch_bounds__(256) batched_kernel(const BatchDesc<T>* __restrict__ descs, int nmat,
-                                                      int total_items) {
-  __shared__ int s_last;
-  for (int item = blockIdx.x; item < total_items; item += gridDim.x) {
-    int lo = 0, hi = nmat - 1;
+__global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __restrict__ descs, int nmat,
+                                                      int total_items, int* __restrict__ next_item) {
+  __shared__ int s_last, s_item;
+  int lo = 0;  // matrix of this CTA's previous item
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total_items) break;
+    int hi = nmat - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (__ldg(&descs[mid].item_begin) <= item)
@@ -116,38 +125,43 @@ __global__ void __launch_bounds__(256) batched_kernel(const BatchDesc<T>* __rest
 }
 
 template <typename T, int VEC, bool SPLIT, int G>
-static cudaError_t batched_go(bool launch, const void* descs, int nmat, int total_items, int grid, size_t smem,
-                              int* blocks_per_sm, cudaStream_t s) {
+static cudaError_t batched_go(bool launch, const void* descs, int nmat, int total_items, int* next_item, int grid,
+                              size_t smem, int* blocks_per_sm, cudaStream_t s) {
   auto kern = batched_kernel<T, VEC, SPLIT, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, 256, smem);
-  kern<<<grid, 256, smem, s>>>(static_cast<const BatchDesc<T>*>(descs), nmat, total_items);
+  kern<<<grid, 256, smem, s>>>(static_cast<const BatchDesc<T>*>(descs), nmat, total_items, next_item);
   return cudaGetLastError();
 }
 
 template <typename T, int VEC>
-static cudaError_t batched_g(bool launch, bool split, int G, const void* descs, int nmat, int total_items, int grid,
-                             size_t smem, int* bps, cudaStream_t s) {
-  if (split) return batched_go<T, 1, true, 1>(launch, descs, nmat, total_items, grid, smem, bps, s);
+static cudaError_t batched_g(bool launch, bool split, int G, const void* descs, int nmat, int total_items,
+                             int* next_item, int grid, size_t smem, int* bps, cudaStream_t s) {
+  if (split) return batched_go<T, 1, true, 1>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
   switch (G) {
-    case 1: return batched_go<T, VEC, false, 1>(launch, descs, nmat, total_items, grid, smem, bps, s);
-    case 2: return batched_go<T, VEC, false, 2>(launch, descs, nmat, total_items, grid, smem, bps, s);
-    case 4: return batched_go<T, VEC, false, 4>(launch, descs, nmat, total_items, grid, smem, bps, s);
-    case 8: return batched_go<T, VEC, false, 8>(launch, descs, nmat, total_items, grid, smem, bps, s);
-    case 16: return batched_go<T, VEC, false, 16>(launch, descs, nmat, total_items, grid, smem, bps, s);
-    case 32: return batched_go<T, VEC, false, 32>(launch, descs, nmat, total_items, grid, smem, bps, s);
+    case 1: return batched_go<T, VEC, false, 1>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
+    case 2: return batched_go<T, VEC, false, 2>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
+    case 4: return batched_go<T, VEC, false, 4>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
+    case 8: return batched_go<T, VEC, false, 8>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
+    case 16: return batched_go<T, VEC, false, 16>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
+    case 32: return batched_go<T, VEC, false, 32>(launch, descs, nmat, total_items, next_item, grid, smem, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t batched_kernel_call(bool launch, int dtype, bool split, int G, bool vec16, const void* descs, int nmat,
-                                int total_items, int grid, size_t smem, int* blocks_per_sm, cudaStream_t s) {
+                                int total_items, int* next_item, int grid, size_t smem, int* blocks_per_sm,
+                                cudaStream_t s) {
   if (dtype == GBS_F64)
-    return vec16 ? batched_g<double, 2>(launch, split, G, descs, nmat, total_items, grid, smem, blocks_per_sm, s)
-                 : batched_g<double, 1>(launch, split, G, descs, nmat, total_items, grid, smem, blocks_per_sm, s);
-  return vec16 ? batched_g<float, 4>(launch, split, G, descs, nmat, total_items, grid, smem, blocks_per_sm, s)
-               : batched_g<float, 1>(launch, split, G, descs, nmat, total_items, grid, smem, blocks_per_sm, s);
+    return vec16 ? batched_g<double, 2>(launch, split, G, descs, nmat, total_items, next_item, grid, smem,
+                                        blocks_per_sm, s)
+                 : batched_g<double, 1>(launch, split, G, descs, nmat, total_items, next_item, grid, smem,
+                                        blocks_per_sm, s);
+  return vec16 ? batched_g<float, 4>(launch, split, G, descs, nmat, total_items, next_item, grid, smem, blocks_per_sm,
+                                     s)
+               : batched_g<float, 1>(launch, split, G, descs, nmat, total_items, next_item, grid, smem, blocks_per_sm,
+                                     s);
 }
 
 }  // namespace gbs

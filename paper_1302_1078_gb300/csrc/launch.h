@@ -85,9 +85,11 @@ cudaError_t launch_sddmm(int dtype, int nnz, int k, const int* rows, const int* 
 
 // Batched persistent kernel (batched.cu).  launch == false: set the shared-memory
 // attribute and report the resident CTAs per SM in *blocks_per_sm; launch == true: launch
-// `grid` CTAs of 256 threads over `descs` (device BatchDesc<T>[nmat]).
+// `grid` CTAs of 256 threads over `descs` (device BatchDesc<T>[nmat]); CTAs claim items
+// from the device counter *next_item, which must be 0 at launch.
 cudaError_t batched_kernel_call(bool launch, int dtype, bool split, int G, bool vec16, const void* descs, int nmat,
-                                int total_items, int grid, size_t smem, int* blocks_per_sm, cudaStream_t s);
+                                int total_items, int* next_item, int grid, size_t smem, int* blocks_per_sm,
+                                cudaStream_t s);
 
 // Message returned by gbs_last_error() on the calling thread (api.cu).
 void set_last_error(const char* msg);
