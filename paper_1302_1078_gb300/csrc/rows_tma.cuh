@@ -165,39 +165,59 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
   const bool col_active = SPLIT ? true : (c_lo < a.k);
   const bool col_full = SPLIT ? true : (c_lo + VEC <= a.k);
   const T* __restrict__ Xc = a.X + c_lo;
-  __shared__ int s_abort;
-  __shared__ T s_red[SPLIT && LANES > 1 ? 256 : 1];
-  if (tid == 0) s_abort = 0;
-  __syncthreads();
+  // row partials of the last two blocks (SpMV with LANES > 1), summed one iteration later
+  __shared__ T s_red[SPLIT && LANES > 1 ? 2 * 256 : 1];
 
-  int i = 0;
-  for (; blk_of(i) < nblocks; ++i) {
-    const int blk = blk_of(i), st = i & 1, slot = i % 3;
-    const uint32_t parity = (uint32_t)((i >> 1) & 1);
-    if (tid == 0 && blk_of(i + 1) < nblocks) issue(blk_of(i + 1), (i + 1) % 3, st ^ 1);
-    int pv0, pv1;
-    load_rp(blk_of(i + 2), pv0, pv1);  // consumed at the end of this iteration
-    if (!mbar_wait_bounded(&bars[st], parity)) {
-      atomicOr(status, 1);
-      s_abort = 1;
-    }
-    const int nr = rows_of(blk);
-    const int* rp = s_rp(slot);
+  // Wait (bounded) for block j's copy in stage j & 1 and add the arrays' last <= 3 nonzeros
+  // with plain loads; returns false on timeout.  The caller's barrier publishes the stage.
+  auto arrive_block = [&](int j) {
+    const int bj = blk_of(j);
+    if (bj >= nblocks) return true;
+    const int st = j & 1;
+    const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((j >> 1) & 1));
+    const int nr = rows_of(bj);
+    const int* rp = s_rp(j % 3);
     const int s = rp[0], e = rp[nr];
     const int a0 = s & ~3;
     int e_cp = (e + 3) & ~3;
     if (e_cp > nnz) e_cp = e & ~3;
-    T* sv = s_val(st);
-    int* sc = s_col(st);
-    if (e_cp < e) {
-      // the arrays' last <= 3 nonzeros: plain loads (block-uniform branch)
-      if (tid < e - e_cp) {
-        sv[e_cp - a0 + tid] = a.vals[e_cp + tid];
-        sc[e_cp - a0 + tid] = a.col_idx[e_cp + tid];
+    if (e_cp < e && tid < e - e_cp) {
+      s_val(st)[e_cp - a0 + tid] = a.vals[e_cp + tid];
+      s_col(st)[e_cp - a0 + tid] = a.col_idx[e_cp + tid];
+    }
+    return ok;
+  };
+  // Row sums of block j from s_red (SpMV with LANES > 1): one thread per row adds the LANES
+  // partials in lane order, so a warp of rows shares each FP64 add.
+  auto finish_rows = [&](int j) {
+    if constexpr (SPLIT && LANES > 1) {
+      const int bj = blk_of(j);
+      const int nr = rows_of(bj);
+      const T* red = s_red + (j & 1) * 256;
+      if (tid < nr) {
+        T sum = red[tid * LANES];
+#pragma unroll
+        for (int l = 1; l < LANES; ++l) sum += red[tid * LANES + l];
+        st_stream(a.Y + (long long)(bj * rpc + tid) * a.ldy, sum);
       }
     }
-    __syncthreads();
-    if (s_abort) break;
+  };
+
+  bool abort = __syncthreads_or(!arrive_block(0)) != 0;
+  int i = 0;
+  for (; !abort && blk_of(i) < nblocks; ++i) {
+    // One barrier per block.  At the top of iteration i, stage i & 1 holds block i (waited
+    // for at the end of the previous iteration) and stage (i + 1) & 1 is free.
+    const int blk = blk_of(i), st = i & 1, slot = i % 3;
+    if (tid == 0 && blk_of(i + 1) < nblocks) issue(blk_of(i + 1), (i + 1) % 3, st ^ 1);
+    int pv0, pv1;
+    load_rp(blk_of(i + 2), pv0, pv1);  // parked at the end of this iteration
+    if (i > 0) finish_rows(i - 1);
+    const int nr = rows_of(blk);
+    const int* rp = s_rp(slot);
+    const int a0 = rp[0] & ~3;
+    const T* sv = s_val(st);
+    const int* sc = s_col(st);
 
     // ---- compute the rows of block blk from stage st
     const bool active = g < nr;
@@ -207,7 +227,62 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
       const int rs = rp[g], re = rp[g + 1];
       constexpr int STEP = SPLIT ? LANES : 1;
       int p = rs + (SPLIT ? lane : 0);
-      if (col_full) {
+      if constexpr (SPLIT && EMUL == 0) {
+        // SpMV: software-pipelined walk of this lane's nonzeros p, p + STEP, ... < re.  The
+        // gathers of group q + 1 are issued before the FMAs of group q wait for theirs, and
+        // the last 0..3 nonzeros are gathered together, so a row costs about one round trip
+        // to L2 per two groups instead of one per group and one per leftover nonzero.  The
+        // products are added in the same order as a plain walk.
+        const int cnt = p < re ? (re - p + STEP - 1) / STEP : 0;
+        const int full = cnt / kUnroll;
+        T va[kUnroll], vb[kUnroll];
+        T xa[kUnroll], xb[kUnroll];
+        auto fetch = [&](int q0, T* v, T* x) {
+          int c[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            v[u] = sv[p + (q0 + u) * STEP - a0];
+            c[u] = sc[p + (q0 + u) * STEP - a0];
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep(Xc + (long long)c[u] * a.ldx, pol_keep);
+        };
+        if (full > 0) {
+          fetch(0, va, xa);
+          int gi = 1;
+          for (; gi + 1 < full; gi += 2) {
+            fetch(gi * kUnroll, vb, xb);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
+            fetch((gi + 1) * kUnroll, va, xa);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[0].add(vb[u], xb[u]);
+          }
+          if (gi < full) {
+            fetch(gi * kUnroll, vb, xb);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[0].add(vb[u], xb[u]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
+          }
+        }
+        const int rem = cnt - full * kUnroll;
+        if (rem > 0) {
+          const int q0 = full * kUnroll;
+#pragma unroll
+          for (int u = 0; u < kUnroll - 1; ++u)
+            if (u < rem) {
+              vb[u] = sv[p + (q0 + u) * STEP - a0];
+              xb[u] = ld_keep(Xc + (long long)sc[p + (q0 + u) * STEP - a0] * a.ldx, pol_keep);
+            }
+#pragma unroll
+          for (int u = 0; u < kUnroll - 1; ++u)
+            if (u < rem) acc[0].add(vb[u], xb[u]);
+        }
+      } else if (col_full) {
         int groups = 0;
         for (; p + (kUnroll - 1) * STEP < re; p += kUnroll * STEP) {
           T v[kUnroll];
@@ -273,17 +348,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
     }
     const int r0 = blk * rpc;
     if constexpr (SPLIT && LANES > 1) {
-      // transposed reduction: the LANES partials of a row go through shared memory and
-      // one thread per row adds them in lane order, so a warp of rows shares each FP64
-      // add instead of every lane paying log2(LANES) shuffled adds
-      s_red[tid] = acc[0].value();
-      __syncthreads();
-      if (tid < nr) {
-        T sum = s_red[tid * LANES];
-#pragma unroll
-        for (int l = 1; l < LANES; ++l) sum += s_red[tid * LANES + l];
-        st_stream(a.Y + (long long)(r0 + tid) * a.ldy, sum);
-      }
+      s_red[st * 256 + tid] = acc[0].value();
     } else if constexpr (SPLIT) {
       if (active) st_stream(a.Y + (long long)(r0 + g) * a.ldy, acc[0].value());
     } else {
@@ -299,15 +364,20 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
       }
     }
     park_rp(blk_of(i + 2), (i + 2) % 3, pv0, pv1);
-    fence_proxy_async_smem();  // generic writes to the stage before the bulk engine reuses it
-    __syncthreads();           // stage st and row slot are free again
+    const bool ok = arrive_block(i + 1);
+    fence_proxy_async_smem();  // generic accesses to stage st before the bulk engine reuses it
+    // stage st, row slot i % 3 and s_red half st ^ 1 are free again; block i + 1 is published
+    abort = __syncthreads_or(!ok) != 0;
   }
-  if (s_abort) {
-    // a wait gave up at iteration i: wait (bounded) for the copies this CTA issued, the
-    // current stage's and, if issued, the next stage's, before the CTA leaves
+  if (abort) {
+    // a wait gave up for block i (i is the block the loop stopped at, waited for after
+    // iteration i - 1 or in the prologue): the only copy this CTA may still have in flight is
+    // block i's, so wait (bounded) for it before the CTA leaves
+    if (tid == 0) atomicOr(status, 1);
     mbar_wait_bounded(&bars[i & 1], (uint32_t)((i >> 1) & 1));
-    if (blk_of(i + 1) < nblocks) mbar_wait_bounded(&bars[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1));
+    return;
   }
+  if (i > 0) finish_rows(i - 1);
 }
 
 }  // namespace gbs
