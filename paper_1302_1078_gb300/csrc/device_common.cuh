@@ -60,6 +60,13 @@ __device__ __forceinline__ uint4 ld_stream_l1_v4(const void* ptr, uint64_t pol) 
   return r;
 }
 
+// Four doubles (one 32-byte sector) in one 256-bit load, L1-allocating; ptr 32-byte aligned.
+__device__ __forceinline__ void ld_stream_l1_4d(const double* ptr, uint64_t pol, double* v) {
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f64 {%0,%1,%2,%3}, [%4], %5;"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(ptr), "l"(pol));
+}
+
 // ---- gathers of the dense operand (reused): L2 evict-last
 __device__ __forceinline__ double ld_keep(const double* ptr, uint64_t pol) {
   double r;

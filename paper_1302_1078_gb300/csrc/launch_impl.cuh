@@ -193,6 +193,7 @@ cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec
   a.perm = PERM ? A.perm : nullptr;
   a.aligned_vals = (reinterpret_cast<uintptr_t>(PERM ? static_cast<const void*>(A.perm) : A.vals) & 15) == 0;
   a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
+  a.vals32 = !PERM && (reinterpret_cast<uintptr_t>(A.vals) & 31) == 0;
   switch (g) {
     case 1: return merge_g<T, 1, PERM>(a, vec16, direct, threads, s);
     case 2: return merge_g<T, 2, PERM>(a, vec16, direct, threads, s);

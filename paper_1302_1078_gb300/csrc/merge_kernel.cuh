@@ -55,6 +55,7 @@ struct MergeArgs {
   int* __restrict__ carry_row;      // [ctas]
   T* __restrict__ carry_val;        // [ctas * k]
   bool aligned_vals, aligned_cols;  // aligned_vals: perm when PERM
+  bool vals32 = false;              // vals 32-byte aligned: a group of four doubles is one 256-bit load
   const int* __restrict__ perm = nullptr;  // PERM: value of entry p is vals[perm[p]]
 };
 
@@ -231,12 +232,16 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
           v[2] = __ldg(a.vals + (int)pw.z);
           v[3] = __ldg(a.vals + (int)pw.w);
         } else if constexpr (sizeof(T) == 8) {
-          const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
-          const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
-          v[0] = __hiloint2double((int)w0.y, (int)w0.x);
-          v[1] = __hiloint2double((int)w0.w, (int)w0.z);
-          v[2] = __hiloint2double((int)w1.y, (int)w1.x);
-          v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+          if (a.vals32) {
+            ld_stream_l1_4d(reinterpret_cast<const double*>(a.vals + nz), pol_stream, reinterpret_cast<double*>(v));
+          } else {
+            const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
+            const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
+            v[0] = __hiloint2double((int)w0.y, (int)w0.x);
+            v[1] = __hiloint2double((int)w0.w, (int)w0.z);
+            v[2] = __hiloint2double((int)w1.y, (int)w1.x);
+            v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+          }
         } else {
           const uint4 w = ld_stream_l1_v4(a.vals + nz, pol_stream);
           v[0] = __uint_as_float(w.x);

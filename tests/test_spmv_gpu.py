@@ -400,3 +400,14 @@ def test_merge_direct_misaligned_values(gbs):
     for items in (3, 31):
         y = gbs.spmv_csr(rp, cm, vm, torch.from_numpy(x).cuda(), config=dict(variant=4, items=items))
         assert_close(y, y_ref, r, torch.float64, f"misaligned direct items={items}")
+    # vals 16-byte but not 32-byte aligned: two 128-bit loads per group instead of one 256-bit
+    vb2 = torch.empty(v.numel() + 4, dtype=torch.float64, device="cuda")
+    v16 = vb2[2:2 + v.numel()]
+    v16.copy_(v)
+    assert v16.data_ptr() % 32 == 16
+    for items in (3, 15, 31):
+        y = gbs.spmv_csr(rp, ci, v16, torch.from_numpy(x).cuda(), config=dict(variant=4, items=items))
+        assert_close(y, y_ref, r, torch.float64, f"16-byte aligned direct items={items}")
+        y32 = gbs.spmv_csr(rp, ci, v, torch.from_numpy(x).cuda(), config=dict(variant=4, items=items))
+        assert torch.equal(y, y32), "the 128-bit and 256-bit load paths must agree bitwise"
+
