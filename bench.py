@@ -491,12 +491,12 @@ def run_batched(args, rank, world, local_rank):
     k = 8
     if args.shard:
         # one batch split across the ranks (strong scaling)
-        specs = synth.batch_specs(512)
+        specs = synth.batch_specs(args.batch_size)
         costs = [sp.rows * (5 if sp.kind == "stencil2d" else sp.avg) for sp in specs]
         mine = shard_for_rank(costs, world, rank)
     else:
         # every rank its own independent batch (weak scaling)
-        specs = synth.batch_specs(512, seed=synth.BASE_SEED + 4 + 1000 * rank)
+        specs = synth.batch_specs(args.batch_size, seed=synth.BASE_SEED + 4 + 1000 * rank)
         mine = list(range(len(specs)))
     mats, Xs, Ys, flops, bytes_ = [], [], [], 0.0, 0
     for i in mine:
@@ -557,7 +557,8 @@ def run_batched(args, rank, world, local_rank):
         "metric": METRIC, "value": flops_all / (ms_b * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
         "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT["batched"], "matrices_per_rank": len(mine),
+        "config": {"workload": WORKLOAD_TEXT["batched"].replace("512", str(args.batch_size)),
+                   "matrices_per_rank": len(mine),
                    "grid": info["grid"], "work_items": info["total_items"], "variants": variants,
                    "l2": "256 MiB write before every step (untimed)"},
         "batched_vs_looped": ms_l / ms_b, "looped_gflops": flops_all / (ms_l * 1e-3) / 1e9,
@@ -647,6 +648,8 @@ def main():
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
+    ap.add_argument("--batch-size", type=int, default=512,
+                    help="batched: matrices per batch (512 is the benchmark configuration; smaller for profiling)")
     ap.add_argument("--emulate", action="store_true",
                     help="let the tuner run part of the FP64 products on the FP32 pipe (float-float, within the "
                          "FP64 accuracy bound); off by default, so the default line is native FP64 arithmetic")
