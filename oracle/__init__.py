@@ -20,6 +20,8 @@ Parity status of each entry point (the pins are in ``tests/test_oracle.py``):
 * ``backward``: pinned by central finite differences of the bilinear loss
   <A X, W> and by dense brute force.
 * ``batch_offsets``: pinned by brute-force running sums.
+* ``ucld``: pinned by the paper's worked example (Sec. 4.1, row 0 19 20 -> 3/16),
+  its two extremes (1/line and 1) and brute force on tiny matrices.
 """
 from __future__ import annotations
 
@@ -65,6 +67,7 @@ def _load():
             lib.orc_backward_f64.argtypes = [i32, i32, i32, P, P, P, P, ll, P, ll, P, ll, P, P, P]
             lib.orc_backward_f32.argtypes = [i32, i32, i32, P, P, P, P, ll, P, ll, P, ll, P, P, P]
             lib.orc_batch_offsets.argtypes = [i32, P, P, P, i32, P, P, P, P, P]
+            lib.orc_ucld.argtypes = [i32, P, P, i32, P, P, P]
             lib.orc_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -170,3 +173,14 @@ def batch_offsets(ms, ns, nnzs, k):
     outs = [np.empty(b + 1, np.int64) for _ in range(5)]
     lib.orc_batch_offsets(int(b), _p(ms), _p(ns), _p(nz), int(k), *[o.ctypes.data for o in outs])
     return tuple(outs)
+
+
+def ucld(m, row_ptr, col_idx, line: int = 8):
+    """(UCLD, sum over rows of distinct x lines, non-empty rows) for aligned lines of
+    ``line`` elements (Sec. 4.1): the mean over non-empty rows of nnz_i / (line * lines_i)."""
+    lib = _load()
+    rp, ci = _c(row_ptr, np.int32), _c(col_idx, np.int32)
+    u = ctypes.c_double()
+    tot, rows = ctypes.c_longlong(), ctypes.c_longlong()
+    lib.orc_ucld(int(m), _p(rp), _p(ci), int(line), ctypes.byref(u), ctypes.byref(tot), ctypes.byref(rows))
+    return u.value, tot.value, rows.value

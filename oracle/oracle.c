@@ -277,6 +277,52 @@ void orc_batch_offsets(int nmat, const int* ms, const int* ns, const long long* 
   off_y[nmat] = yo;
 }
 
+/* ------------------------------------------------------------------ UCLD */
+
+static int cmp_int(const void* a, const void* b) {
+  const int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Useful cacheline density (Sec. 4.1, the figure relating vectorised SpMV
+ * speed to it): x is cut into aligned lines of `line` elements (line j holds
+ * x[j*line .. j*line+line-1]).  For a non-empty row i with nnz_i nonzeros
+ * whose columns touch lines_i distinct lines, the row's density is
+ *     nnz_i / (line * lines_i),
+ * and UCLD is the mean of that ratio over the non-empty rows (an empty row
+ * has no ratio; the paper is silent on it).  The paper's example: columns 0,
+ * 19 and 20 with 8-element lines touch lines 0 and 2, so the row's density
+ * is 3 / 16.  Also returned: the sum of lines_i over all rows (the line
+ * fetches of one pass over x if no line were reused between rows) and the
+ * number of non-empty rows.  Distinct lines are counted by sorting a copy of
+ * the row's line ids, so unsorted or repeated columns are handled.
+ */
+void orc_ucld(int m, const int* rptrs, const int* cids, int line, double* ucld, long long* lines_total,
+              long long* nonempty) {
+  long long maxlen = 0;
+  for (int i = 0; i < m; ++i)
+    if (rptrs[i + 1] - rptrs[i] > maxlen) maxlen = rptrs[i + 1] - rptrs[i];
+  int* buf = (int*)malloc(sizeof(int) * (size_t)(maxlen > 0 ? maxlen : 1));
+  double sum = 0.0;
+  long long tot = 0, rows = 0;
+  for (int i = 0; i < m; ++i) {
+    const int len = rptrs[i + 1] - rptrs[i];
+    if (len == 0) continue;
+    for (int q = 0; q < len; ++q) buf[q] = cids[rptrs[i] + q] / line;
+    qsort(buf, (size_t)len, sizeof(int), cmp_int);
+    long long distinct = 1;
+    for (int q = 1; q < len; ++q) distinct += buf[q] != buf[q - 1];
+    sum += (double)len / ((double)line * (double)distinct);
+    tot += distinct;
+    rows += 1;
+  }
+  free(buf);
+  *ucld = rows > 0 ? sum / (double)rows : 0.0;
+  *lines_total = tot;
+  *nonempty = rows;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP

@@ -369,6 +369,117 @@ def test_batch_offsets_brute_force():
     assert (off_rows[37], off_nnz[37], off_rp[37], off_x[37], off_y[37]) == (r, z, rp, xo, yo)
 
 
+# ------------------------------------------------------------------ UCLD
+
+def _ucld_rows(rows, line):
+    rp = np.zeros(len(rows) + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([c for r in rows for c in r], np.int32)
+    return oracle.ucld(len(rows), rp, ci, line)
+
+
+def test_ucld_paper_example():
+    """The worked example and the extremes of Sec. 4.1 (tests/golden/ucld_example.txt)."""
+    from fractions import Fraction
+    for line in open(os.path.join(GOLDEN, "ucld_example.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        cols, L, num, den = line.split()
+        cols = [int(c) for c in cols.split(",")]
+        u, lines, rows = _ucld_rows([cols], int(L))
+        assert Fraction(u).limit_denominator(1000) == Fraction(int(num), int(den))
+        assert rows == 1
+    # the example's two lines, and order does not matter
+    assert _ucld_rows([[20, 0, 19]], 8)[:2] == (3 / 16, 2)
+
+
+def test_ucld_closed_forms():
+    # identity: one nonzero per row on its own line -> 1 / line
+    n = 1000
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    for L in (4, 8, 16):
+        u, lines, rows = oracle.ucld(n, rp, ci, L)
+        assert u == pytest.approx(1.0 / L, rel=1e-15) and lines == n and rows == n
+    # a dense aligned 64-column row -> 1; empty rows are skipped
+    u, lines, rows = _ucld_rows([[], list(range(64)), []], 8)
+    assert (u, lines, rows) == (1.0, 8, 1)
+    # 2D 5-point stencil, interior row i on an N x N grid with 8-element lines: the
+    # vertical neighbours i +- N sit on their own lines (N >= 8), and i-1, i, i+1 share
+    # one line unless i is first or last in its line
+    N = 64
+    A = synth.stencil2d(N)
+    u, lines, rows = oracle.ucld(A.m, A.row_ptr, A.col_idx, 8)
+    want = 0.0
+    for i in range(A.m):
+        r, c = divmod(i, N)
+        cols = [i] + ([i - N] if r > 0 else []) + ([i + N] if r < N - 1 else []) + \
+               ([i - 1] if c > 0 else []) + ([i + 1] if c < N - 1 else [])
+        lines_i = len({x // 8 for x in cols})
+        want += len(cols) / (8 * lines_i)
+    assert u == pytest.approx(want / A.m, rel=1e-13)
+
+
+def test_ucld_brute_force():
+    rng = np.random.default_rng(70)
+    for trial in range(20):
+        A = synth.random_csr(int(rng.integers(1, 60)), int(rng.integers(1, 200)), float(rng.uniform(0, 0.3)),
+                             100 + trial, sorted_cols=bool(trial % 2), duplicates=bool(trial % 3 == 0),
+                             empty_rows=0.2)
+        for L in (1, 4, 8, 16):
+            s, tot, rows = 0.0, 0, 0
+            for i in range(A.m):
+                cols = A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]]
+                if cols.size == 0:
+                    continue
+                d = np.unique(cols // L).size
+                s += cols.size / (L * d)
+                tot += d
+                rows += 1
+            u, lines, nrows = oracle.ucld(A.m, A.row_ptr, A.col_idx, L)
+            assert (lines, nrows) == (tot, rows)
+            assert u == pytest.approx(s / rows if rows else 0.0, rel=1e-14, abs=0.0)
+
+
+UCLD_MUTATIONS = [
+    ("runs instead of distinct lines", "qsort(buf, (size_t)len, sizeof(int), cmp_int);", ";"),
+    ("line factor dropped", "sum += (double)len / ((double)line * (double)distinct);",
+     "sum += (double)len / ((double)distinct);"),
+    ("empty rows counted", "if (len == 0) continue;", "if (len == 0) { rows += 1; continue; }"),
+    ("element index instead of line", "buf[q] = cids[rptrs[i] + q] / line;", "buf[q] = cids[rptrs[i] + q];"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", UCLD_MUTATIONS, ids=[m[0] for m in UCLD_MUTATIONS])
+def test_ucld_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert old in src
+    c = tmp_path / "mut.c"
+    c.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.orc_ucld.argtypes = [i32, P, P, i32, P, P, P]
+
+    def mutant(m, rp, ci, line):
+        rp = np.ascontiguousarray(rp, np.int32)
+        ci = np.ascontiguousarray(ci, np.int32)
+        u, tot, rows = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        lib.orc_ucld(int(m), rp.ctypes.data, ci.ctypes.data if ci.size else 0, int(line), ctypes.byref(u),
+                     ctypes.byref(tot), ctypes.byref(rows))
+        return u.value, tot.value, rows.value
+
+    monkeypatch.setattr(oracle, "ucld", mutant)
+    caught = 0
+    for check in (test_ucld_paper_example, test_ucld_closed_forms, test_ucld_brute_force):
+        try:
+            check()
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, f"no pin caught the planted mistake: {name}"
+
+
 # ---------------------------------------------- planted mistakes (mutation)
 
 MUTATIONS = [
