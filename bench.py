@@ -183,13 +183,14 @@ def gpu_smi_id(torch, dev_index: int) -> str:
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(mats, ks, budget_s: float = 12.0, frac_rows: float | None = None):
-    """Time the CPU oracle (paper Sec. 4.1 row-parallel loop, all host cores) on the workload's
-    matrices, repeating whole sweeps until `budget_s` is spent (at least one sweep, over a
-    leading fraction of the rows if `frac_rows` is given).  Returns (GFLOP/s, cores, text)."""
+def cpu_oracle_rate(mats, ks, budget_s: float = 12.0, frac_rows: float | None = None, threads: int | None = None):
+    """Time the CPU oracle (paper Sec. 4.1 row-parallel loop, all host cores unless `threads`)
+    on the workload's matrices, repeating whole sweeps until `budget_s` is spent (at least one
+    sweep, over a leading fraction of the rows if `frac_rows` is given).
+    Returns (GFLOP/s, cores, text)."""
     import oracle
 
-    threads = oracle.max_threads()
+    threads = oracle.max_threads() if threads is None else threads
     xs = {}
     flops = 0.0
     t_total = 0.0
@@ -300,13 +301,17 @@ def run_gpu(args, rank, world, local_rank):
         rp = torch.from_numpy(A.row_ptr).to(dev)
         ci = torch.from_numpy(A.col_idx).to(dev)
         v = torch.from_numpy(A.vals).to(dev)
+        # useful cacheline density of the x gathers (Sec. 4.1): 4 doubles = one 32-byte L2 sector,
+        # 8 = the paper's 64-byte line; "x_sectors" = distinct sectors summed over rows
+        u4, u8 = gbs.ucld(rp, ci, A.n, 4), gbs.ucld(rp, ci, A.n, 8)
+        ucld = {"sector_4": u4["ucld"], "line_8": u8["ucld"], "x_sectors": u4["lines"]}
         for k in ks:
             X = synth.uniform(A.n * k, seed=synth.BASE_SEED + 11 + rank, stream=k)
             Xd = torch.from_numpy(X).to(dev).reshape(A.n, k) if k > 1 else torch.from_numpy(X).to(dev)
             Yd = torch.empty((A.m, k) if k > 1 else (A.m,), dtype=torch.float64, device=dev)
             plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True, emulate=args.emulate)
             items.append(dict(name=name, A=A, k=k, rp=rp, ci=ci, v=v, X=Xd, Y=Yd, plan=plan, cfg=plan.config,
-                              bytes=compulsory_bytes(A.m, A.n, A.nnz, k), flops=2.0 * A.nnz * k))
+                              bytes=compulsory_bytes(A.m, A.n, A.nnz, k), flops=2.0 * A.nnz * k, ucld=ucld))
     stream = torch.cuda.current_stream(dev)
 
     def call(it):
@@ -363,6 +368,19 @@ def run_gpu(args, rank, world, local_rank):
     sampler.stop()
     per_item_ms = [[ev[s][j][0].elapsed_time(ev[s][j][1]) for s in range(args.steps)] for j in range(len(items))]
     step_ms = sum(statistics.mean(t) for t in per_item_ms)
+
+    # ---- warm figure (labelled, not the value): the same products back to back, no L2 flush
+    warm_steps = max(3, min(args.steps, 20))
+    wev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in items]
+           for _ in range(warm_steps)]
+    for s in range(warm_steps):
+        for j, it in enumerate(items):
+            wev[s][j][0].record(stream)
+            call(it)
+            wev[s][j][1].record(stream)
+    torch.cuda.synchronize(dev)
+    warm_ms = [statistics.mean(wev[s][j][0].elapsed_time(wev[s][j][1]) for s in range(warm_steps))
+               for j in range(len(items))]
     flops_step = sum(it["flops"] for it in items)
 
     # ---- end to end through the public API with host buffers (H2D inputs, D2H result, each step)
@@ -418,7 +436,8 @@ def run_gpu(args, rank, world, local_rank):
         per.append({"matrix": it["name"], "k": it["k"], "m": it["A"].m, "nnz": it["A"].nnz, "config": it["cfg"],
                     "ms": ms, "gflops": it["flops"] / ms / 1e6, "hbm_gbs": it["bytes"] / ms / 1e6,
                     "hbm_frac": it["bytes"] / ms / 1e6 / hbm_peak,
-                    "fp64_frac": it["flops"] / ms / 1e6 / fp64_peak_gflops})
+                    "fp64_frac": it["flops"] / ms / 1e6 / fp64_peak_gflops,
+                    "warm_ms_no_l2_flush": warm_ms[j], "ucld": it["ucld"]})
     dom = max(range(len(items)), key=lambda j: per[j]["ms"])
     d = per[dom]
     t_hbm = items[dom]["bytes"] / (hbm_peak * 1e9)
@@ -456,6 +475,8 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, what = cpu_oracle_rate(mats, ks)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": what}
+        v1, _, what1 = cpu_oracle_rate(mats, ks, budget_s=4.0, threads=1)
+        line["cpu_baseline_1core"] = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -145,6 +145,24 @@ int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out
  */
 int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream);
 
+/*
+ * Diagnostic: useful cacheline density (UCLD, Sec. 4.1, the figure that ties
+ * the gain of vectorised SpMV to it).  x is cut into aligned lines of
+ * `line_elems` elements (line j = x[j*line_elems .. (j+1)*line_elems - 1]); a
+ * non-empty row i with nnz_i nonzeros whose columns touch lines_i distinct
+ * lines has density nnz_i / (line_elems * lines_i).  Writes to host pointers
+ * (each may be NULL): *ucld = the mean density over non-empty rows (0 if
+ * none; computed in 2^-31 fixed point, so within 5e-10 of the exact mean),
+ * *lines = sum of lines_i over the rows (the line fetches of x if no line were
+ * reused between rows), *nonempty_rows.  The paper's example: columns 0, 19,
+ * 20 with 8-element lines give 3/16.  line_elems = 4 is GB300's 32-byte L2
+ * sector of doubles.  Unsorted or repeated columns are counted correctly (an
+ * unsorted row costs time quadratic in its length).  Synchronises `stream`.
+ * Errors: GBS_EINVAL (line_elems < 1, bad sizes, NULL arrays).
+ */
+int gbs_ucld(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int line_elems, double* ucld,
+             long long* lines, long long* nonempty_rows, void* stream);
+
 /* ------------------------------------------------------------------ SpMV */
 /*
  * y <- A x  (Sec. 3).  vals, x and y have type `dtype`; x has n entries and

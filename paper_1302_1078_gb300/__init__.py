@@ -140,6 +140,21 @@ def csr_stats(row_ptr, n: int, nnz: int | None = None, stream=None) -> dict:
     return st.as_dict()
 
 
+def ucld(row_ptr, col_idx, n: int, line_elems: int = 8, stream=None) -> dict:
+    """Useful cacheline density (Sec. 4.1) for aligned x lines of ``line_elems`` elements:
+    {"ucld": mean over non-empty rows of nnz_i / (line_elems * lines_i), "lines": sum of lines_i,
+    "nonempty_rows": ...}, computed on the device."""
+    _check_index(row_ptr, col_idx)
+    dev = _need_cuda(row_ptr, col_idx)
+    m = row_ptr.numel() - 1
+    u = ctypes.c_double()
+    tot, rows = ctypes.c_longlong(), ctypes.c_longlong()
+    _capi.check(lib().gbs_ucld(m, int(n), col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), int(line_elems),
+                               ctypes.byref(u), ctypes.byref(tot), ctypes.byref(rows), _stream(dev, stream)),
+                "gbs_ucld")
+    return {"ucld": u.value, "lines": tot.value, "nonempty_rows": rows.value}
+
+
 def validate_csr(row_ptr, col_idx, n: int, stream=None) -> None:
     """Raise GbsError(GBS_EINDEX) if the CSR structure is malformed."""
     dev = _need_cuda(row_ptr, col_idx)

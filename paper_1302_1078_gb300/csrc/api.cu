@@ -484,6 +484,31 @@ int gbs_csr_stats(int m, int n, int nnz, const int* row_ptr, gbs_stats* out, voi
   return compute_stats(m, n, nnz, row_ptr, out, static_cast<cudaStream_t>(stream));
 }
 
+int gbs_ucld(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int line_elems, double* ucld,
+             long long* lines, long long* nonempty_rows, void* stream) {
+  int rc = check_csr(m, n, nnz, row_ptr, col_idx, reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  if (line_elems < 1) return fail(GBS_EINVAL, "line_elems must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long h[3] = {0, 0, 0};
+  if (m > 0 && nnz > 0) {
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(h), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (ucld)");
+    e = cudaMemsetAsync(d, 0, sizeof(h), s);
+    if (e == cudaSuccess) e = launch_ucld(row_ptr, col_idx, m, line_elems, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ucld");
+  }
+  if (ucld) *ucld = h[2] ? (double)h[0] / 2147483648.0 / (double)h[2] : 0.0;
+  if (lines) *lines = (long long)h[1];
+  if (nonempty_rows) *nonempty_rows = (long long)h[2];
+  return GBS_OK;
+}
+
 int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out) {
   if (stats == nullptr || out == nullptr) return fail(GBS_EINVAL, "NULL pointer");
   if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");

@@ -91,6 +91,11 @@ cudaError_t batched_kernel_call(bool launch, int dtype, bool split, int G, bool 
                                 int total_items, int* next_item, int grid, size_t smem, int* blocks_per_sm,
                                 cudaStream_t s);
 
+// UCLD sums (ucld.cu): acc[0] += sum of nnz_i / (line * lines_i) over non-empty rows in 2^-31
+// fixed point, acc[1] += sum of lines_i, acc[2] += non-empty rows.
+cudaError_t launch_ucld(const int* row_ptr, const int* col_idx, int m, int line, unsigned long long* acc,
+                        cudaStream_t s);
+
 // Message returned by gbs_last_error() on the calling thread (api.cu).
 void set_last_error(const char* msg);
 

@@ -63,6 +63,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gbs_plan_create(None, 1, 1, 0, None, None, 0, 1, 0, None) == _capi.GBS_EINVAL
     cfg = _capi.gbs_config(variant=1, lanes=3, threads=256, tile_nnz=2048, items=0)
     assert lib.spmv_csr_cfg(4, 4, 0, 16, None, None, 0, 16, 16, ctypes.byref(cfg), None) == _capi.GBS_EINVAL
+    assert lib.gbs_ucld(4, 4, 0, 16, None, 0, None, None, None, None) == _capi.GBS_EINVAL  # line_elems < 1
+    assert lib.gbs_ucld(-1, 4, 0, None, None, 8, None, None, None, None) == _capi.GBS_EINVAL
+    assert lib.gbs_tplan_set_config(None, 0, 1, None, None) == _capi.GBS_EINVAL
 
 
 def test_default_config_host_only(lib):
