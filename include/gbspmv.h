@@ -283,7 +283,7 @@ int gbs_tplan_destroy(gbs_tplan* plan);
  * Make (and keep) a plan of A^T for `dtype` and k, with gbs_plan_create's
  * flags (GBS_PLAN_TUNE to autotune it); spmv_csr_backward then computes dX with
  * that plan's configuration instead of the one picked from A^T's row
- * statistics.  dX reads A's values in place through perm (ROWS or
+ * statistics.  dX reads A's values in place through perm (ROWS, MERGE or
  * MERGE_DIRECT); with GBS_PLAN_TUNE the tuner also times permuting the
  * values into scratch first (one extra pass) followed by the best of all
  * variants, and keeps that route if it is faster.  Synchronises `stream`.
@@ -292,8 +292,8 @@ int gbs_tplan_destroy(gbs_tplan* plan);
 int gbs_tplan_prepare(gbs_tplan* plan, int dtype, int k, int flags, void* stream);
 /*
  * Set the configuration of dX for (dtype, k), replacing a prepared one.
- * GBS_VARIANT_ROWS and GBS_VARIANT_MERGE_DIRECT read A's values in place
- * through perm; GBS_VARIANT_ROWS_TMA and GBS_VARIANT_MERGE permute them into
+ * GBS_VARIANT_ROWS, GBS_VARIANT_MERGE and GBS_VARIANT_MERGE_DIRECT read A's
+ * values in place through perm; GBS_VARIANT_ROWS_TMA permutes them into
  * plan-owned scratch first (allocated here, nnz doubles); GBS_VARIANT_AUTO
  * takes the configuration from A^T's row statistics.  Errors as
  * gbs_plan_set_config.  Synchronises `stream`.

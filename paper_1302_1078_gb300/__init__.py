@@ -280,8 +280,8 @@ class TransposePlan:
                                             _stream(self.device, stream)), "gbs_tplan_prepare")
 
     def set_config(self, dtype, k: int, cfg, stream=None) -> None:
-        """Configuration of dX = A^T dY for dtype and k.  ROWS and MERGE_DIRECT read A's values in
-        place through the transpose permutation; ROWS_TMA and MERGE permute them first."""
+        """Configuration of dX = A^T dY for dtype and k.  ROWS, MERGE and MERGE_DIRECT read A's
+        values in place through the transpose permutation; ROWS_TMA permutes them first."""
         dt = _capi.GBS_F64 if dtype == torch.float64 else _capi.GBS_F32
         _capi.check(lib().gbs_tplan_set_config(self._h, dt, int(k), ctypes.byref(_config(cfg)),
                                                _stream(self.device, stream)), "gbs_tplan_set_config")

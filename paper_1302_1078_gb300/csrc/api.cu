@@ -169,8 +169,8 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
   const size_t es = dsize(dtype);
   cudaError_t e = cudaSuccess;
   const bool perm = A.perm != nullptr;
-  if (perm && cfg.variant != GBS_VARIANT_ROWS && cfg.variant != GBS_VARIANT_MERGE_DIRECT)
-    return fail(GBS_EUNSUPPORTED, "values read through a permutation need the ROWS or MERGE_DIRECT variant");
+  if (perm && cfg.variant == GBS_VARIANT_ROWS_TMA)
+    return fail(GBS_EUNSUPPORTED, "values read through a permutation need the ROWS, MERGE or MERGE_DIRECT variant");
   if (cfg.variant == GBS_VARIANT_ROWS_TMA && status && aligned16(A.vals) && aligned16(A.col_idx)) {
     for (int c0 = 0; c0 < k; c0 += P) {
       const int kp = std::min(P, k - c0);
@@ -713,7 +713,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     // values through a permutation: the variants that support it
     std::vector<gbs_config> keep;
     for (const gbs_config& g : c)
-      if ((g.variant == GBS_VARIANT_ROWS || g.variant == GBS_VARIANT_MERGE_DIRECT) && g.emul == 0) keep.push_back(g);
+      if (g.variant != GBS_VARIANT_ROWS_TMA && g.emul == 0) keep.push_back(g);
     c.swap(keep);
   }
   return c;
@@ -814,6 +814,9 @@ int plan_create_impl(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr,
   rc = compute_stats(m, n, nnz, row_ptr, &p->stats, s);
   if (rc == GBS_OK) {
     p->cfg = heuristic_config(p->stats, dtype, k);
+    // values through a permutation: the direct merge form gathers them in its walk, with
+    // more of them in flight than the staged form's synchronous gather (the tuner may still
+    // pick the staged form)
     if (perm && p->cfg.variant == GBS_VARIANT_MERGE) p->cfg.variant = GBS_VARIANT_MERGE_DIRECT;
     rc = (flags & GBS_PLAN_TUNE) && m > 0 ? plan_tune(p, s) : plan_prepare(p, s);
   }
@@ -1097,7 +1100,7 @@ int gbs_tplan_set_config(gbs_tplan* t, int dtype, int k, const gbs_config* cfg, 
   if (!t || !cfg) return fail(GBS_EINVAL, "NULL pointer");
   if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
   if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
-  const bool gather = cfg->variant == GBS_VARIANT_ROWS_TMA || cfg->variant == GBS_VARIANT_MERGE;
+  const bool gather = cfg->variant == GBS_VARIANT_ROWS_TMA;
   gbs_plan* p = nullptr;
   int rc = plan_create_impl(&p, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, 0, gather ? nullptr : t->perm,
                             stream);

@@ -157,6 +157,32 @@ __device__ __forceinline__ void stage_copy(E* __restrict__ s, const E* __restric
   }
 }
 
+// s[0 .. c1 - a0) = vals[perm[a0 .. c1)] with the whole CTA: the permutation is read with
+// 128-bit streaming loads when `aligned` (perm 16-byte aligned; a0 is a multiple of 4), and
+// each thread then has four independent value gathers in flight.
+template <typename T>
+__device__ __forceinline__ void stage_gather(T* __restrict__ s, const T* __restrict__ vals,
+                                             const int* __restrict__ perm, int a0, int c1, bool aligned,
+                                             uint64_t pol) {
+  const int cnt = c1 - a0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int done = 0;
+  if (aligned) {
+    const int nvec = cnt / 4;
+    for (int q = tid; q < nvec; q += nt) {
+      const uint4 w = ld_stream_v4(perm + a0 + 4 * q, pol);
+      const T v0 = __ldg(vals + (int)w.x), v1 = __ldg(vals + (int)w.y);
+      const T v2 = __ldg(vals + (int)w.z), v3 = __ldg(vals + (int)w.w);
+      s[4 * q] = v0;
+      s[4 * q + 1] = v1;
+      s[4 * q + 2] = v2;
+      s[4 * q + 3] = v3;
+    }
+    done = nvec * 4;
+  }
+  for (int q = done + tid; q < cnt; q += nt) s[q] = __ldg(vals + ld_stream(perm + a0 + q, pol));
+}
+
 // Accumulator for one output element.  double: plain fused multiply-add in
 // double.  float: the product is rounded once and added with Knuth's TwoSum,
 // the rounding errors collected in a second float (compensated summation), so

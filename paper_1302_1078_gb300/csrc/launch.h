@@ -10,7 +10,7 @@ struct CsrView {
   const int* row_ptr;
   const int* col_idx;
   const void* vals;
-  const int* perm = nullptr;  // if set, the value of entry p is vals[perm[p]] (ROWS, MERGE_DIRECT only)
+  const int* perm = nullptr;  // if set, the value of entry p is vals[perm[p]] (ROWS, MERGE, MERGE_DIRECT)
 };
 
 struct DenseView {
@@ -54,7 +54,7 @@ cudaError_t launch_merge_f64(const CsrView& A, const DenseView& D, int g, bool v
 cudaError_t launch_merge_f32(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
                              int items, const MergeScratch& S, cudaStream_t s);
 // The same launchers for a CsrView whose values are read through A.perm (the backward pass's
-// A^T on A's values); the merge form must be direct.
+// A^T on A's values).
 cudaError_t launch_rows_perm_f64(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
                                  int row_base, int rows, cudaStream_t s);
 cudaError_t launch_rows_perm_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,

@@ -161,15 +161,11 @@ static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, bool direct, int t
     if (vec16 && a.k > 1) return merge_go<T, V, G, true, PERM>(a, threads, s);
     return merge_go<T, 1, G, true, PERM>(a, threads, s);
   }
-  if constexpr (PERM) {
-    return cudaErrorInvalidValue;  // permuted values: direct form only
-  } else {
-    if (vec16 && a.k > 1) return merge_go<T, V, G, false, false>(a, threads, s);
-    return merge_go<T, 1, G, false, false>(a, threads, s);
-  }
+  if (vec16 && a.k > 1) return merge_go<T, V, G, false, PERM>(a, threads, s);
+  return merge_go<T, 1, G, false, PERM>(a, threads, s);
 }
 
-// PERM: A.perm is set and the value of entry p is A.vals[A.perm[p]] (direct form only).
+// PERM: A.perm is set and the value of entry p is A.vals[A.perm[p]].
 template <typename T, bool PERM = false>
 cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec16, bool direct, int threads,
                            int items, const MergeScratch& S, cudaStream_t s) {

@@ -33,8 +33,10 @@
 //     direct form needs only the row-pointer window in shared memory (4 bytes
 //     per item instead of 16), which allows more items per thread at the same
 //     residency and spreads the carry scan over more nonzeros.
-//   * PERM (direct form only): the value of stored entry p is vals[perm[p]],
-//     so the backward pass can run A^T on A's values without a permuted copy.
+//   * PERM: the value of stored entry p is vals[perm[p]], so the backward
+//     pass can run A^T on A's values without a permuted copy.  The staged
+//     form gathers the tile's values into shared memory (perm read with
+//     128-bit loads); the direct form gathers them in its walk.
 #pragma once
 #include "device_common.cuh"
 
@@ -92,7 +94,6 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
 // standalone kernel below and by the batched persistent kernel.
 template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false>
 __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
-  static_assert(!PERM || DIRECT, "permuted values need the direct form");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = blockDim.x / G;
   const int nw = blockDim.x / 32;
@@ -123,7 +124,10 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   for (int q = threadIdx.x; q < nrp; q += blockDim.x) s_rp[q] = ld_stream(a.row_ptr + row0 + q, pol_stream);
   const int a0 = nz0 & ~3;
   if (!DIRECT && nz1 > nz0) {
-    stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
+    if constexpr (PERM)
+      stage_gather<T>(s_val, a.vals, a.perm, a0, nz1, a.aligned_vals, pol_stream);
+    else
+      stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
     stage_copy<int>(s_col, a.col_idx, a0, nz1, a.aligned_cols, pol_stream);
   }
   __syncthreads();

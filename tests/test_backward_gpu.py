@@ -110,9 +110,10 @@ AT_CONFIGS = [
     dict(variant=V["MERGE_DIRECT"], threads=256, items=31),
     dict(variant=V["MERGE_DIRECT"], threads=64, items=7),
     dict(variant=V["MERGE_DIRECT"], threads=128, items=63),
+    dict(variant=V["MERGE"], threads=256, items=11),
+    dict(variant=V["MERGE"], threads=128, items=7),
     # values permuted into scratch first
     dict(variant=V["ROWS_TMA"], lanes=2, threads=64),
-    dict(variant=V["MERGE"], threads=256, items=11),
 ]
 
 
@@ -176,7 +177,7 @@ def test_backward_config_errors(gbs):
         t.set_config(torch.float64, 0, dict(variant=V["ROWS"]))
     # AUTO: the statistics-based configuration, values in place
     t.set_config(torch.float64, 1, dict(variant=0))
-    assert t.config(torch.float64, 1)["variant"] in (V["ROWS"], V["MERGE_DIRECT"])
+    assert t.config(torch.float64, 1)["variant"] in (V["ROWS"], V["MERGE"], V["MERGE_DIRECT"])
 
 
 def test_autograd_gradcheck(gbs):
