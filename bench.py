@@ -533,6 +533,8 @@ def run_batched(args, rank, world, local_rank):
         bytes_ += compulsory_bytes(A.m, A.n, A.nnz, k)
     plan = gbs.BatchedPlan(mats, Xs, Ys, tune=True)
     info = plan.info()
+    # the baseline a per-matrix user would run: each matrix's own standalone-tuned configuration
+    plan_pm = gbs.BatchedPlan(mats, Xs, Ys, tune=True, configs=[None] * len(mats))
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -549,6 +551,7 @@ def run_batched(args, rank, world, local_rank):
     for _ in range(args.warmup):
         plan.run()
         plan.run_looped()
+        plan_pm.run_looped()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(gpu_smi_id(torch, local_rank))
     if world > 1:
@@ -559,14 +562,15 @@ def run_batched(args, rank, world, local_rank):
     t_batched = timed(plan.run, args.steps)
     torch.cuda.nvtx.range_pop()
     t_looped = timed(plan.run_looped, args.steps)
+    t_looped_pm = timed(plan_pm.run_looped, args.steps)
     sampler.stop()
-    ms_b, ms_l = statistics.mean(t_batched), statistics.mean(t_looped)
-    t = torch.tensor([ms_b, ms_l], dtype=torch.float64, device=dev)
+    ms_b, ms_l, ms_lpm = statistics.mean(t_batched), statistics.mean(t_looped), statistics.mean(t_looped_pm)
+    t = torch.tensor([ms_b, ms_l, ms_lpm], dtype=torch.float64, device=dev)
     tot = torch.tensor([flops, float(bytes_)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    ms_b, ms_l = float(t[0]), float(t[1])
+    ms_b, ms_l, ms_lpm = float(t[0]), float(t[1]), float(t[2])
     flops_all, bytes_all = float(tot[0]), float(tot[1])
     hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
@@ -584,6 +588,9 @@ def run_batched(args, rank, world, local_rank):
                    "l2": "256 MiB write before every step (untimed)"},
         "batched_vs_looped": ms_l / ms_b, "looped_gflops": flops_all / (ms_l * 1e-3) / 1e9,
         "looped_ms": ms_l,
+        "looped_note": "looped = the batch's own per-matrix configurations, one launch per matrix; "
+                       "looped_tuned = each matrix's standalone-tuned configuration, one launch per matrix",
+        "batched_vs_looped_tuned": ms_lpm / ms_b, "looped_tuned_ms": ms_lpm,
         "roofline": {"bound": "hbm", "achieved": bytes_all / (ms_b * 1e-3) / 1e9 / world, "peak": hbm_peak,
                      "unit": "GB/s", "frac": bytes_all / (ms_b * 1e-3) / 1e9 / world / hbm_peak, "traffic": None,
                      "kernel": "batched_kernel (whole batch per launch)"},

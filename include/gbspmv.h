@@ -326,7 +326,9 @@ int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, c
  *   - picks each matrix's configuration (ROWS lanes / tile or MERGE items;
  *     256 threads) from its row statistics, or with GBS_PLAN_TUNE by timing
  *     candidates with standalone launches on the given operands (this
- *     writes Y_b);
+ *     writes Y_b), and then by timing a few whole-batch policies on the
+ *     batched kernel itself (the statistics' variant with larger ROWS tiles;
+ *     MERGE for matrices of short rows), keeping the fastest plan;
  *   - builds the work list: matrix b owns the contiguous items
  *     [item_begin[b], item_begin[b+1]) (row blocks or merge tiles); the
  *     grid is every resident CTA slot (`grid`), and each CTA claims the next
@@ -356,6 +358,19 @@ typedef struct gbs_batch_plan gbs_batch_plan;
 
 int spmv_csr_batched_plan(gbs_batch_plan** plan, int nmat, const gbs_batch_item* items /* host */, int dtype,
                           int k, int flags, void* stream);
+/*
+ * The same plan with the caller's per-matrix configurations: cfgs (host,
+ * nmat entries) gives each matrix GBS_VARIANT_ROWS or GBS_VARIANT_MERGE with
+ * its lanes (k == 1; k > 1 uses the batch's column lanes), tile_nnz or items,
+ * or GBS_VARIANT_AUTO for the heuristic / tuner choice of
+ * spmv_csr_batched_plan.  threads is always 256; merge items are capped to the
+ * batch kernel's shared-memory budget (spmv_csr_batched_info reports the values
+ * used).  Errors: GBS_EUNSUPPORTED (another variant), GBS_EINVAL (as
+ * gbs_plan_set_config).  cfgs == NULL is spmv_csr_batched_plan.
+ */
+int spmv_csr_batched_plan_cfg(gbs_batch_plan** plan, int nmat, const gbs_batch_item* items /* host */,
+                              int dtype, int k, int flags, const gbs_config* cfgs /* host, may be NULL */,
+                              void* stream);
 /*
  * Launch the captured graph on `stream`.  X and Y (host arrays of nmat device
  * pointers, or NULL to keep the current ones) replace the dense operands

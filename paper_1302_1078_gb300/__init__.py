@@ -390,7 +390,7 @@ class BatchedPlan:
     ``mats``: list of (row_ptr, col_idx, vals, n); ``X``/``Y``: lists of dense operands
     (1-D for k == 1, else n x k / m x k row major).  Keeps references to every tensor."""
 
-    def __init__(self, mats, X, Y, *, tune: bool = False, check: bool = False, stream=None):
+    def __init__(self, mats, X, Y, *, tune: bool = False, check: bool = False, configs=None, stream=None):
         if not (len(mats) == len(X) == len(Y)) or not mats:
             raise ValueError("mats, X and Y must be non-empty lists of equal length")
         self.nmat = len(mats)
@@ -416,8 +416,20 @@ class BatchedPlan:
         self._items = arr
         self._h = ctypes.c_void_p()
         flags = (_capi.PLAN_TUNE if tune else 0) | (_capi.PLAN_CHECK if check else 0)
-        _capi.check(lib().spmv_csr_batched_plan(ctypes.byref(self._h), self.nmat, arr, _dtype_code(mats[0][2]),
-                                                self.k, flags, _stream(dev, stream)), "spmv_csr_batched_plan")
+        if configs is None:
+            _capi.check(lib().spmv_csr_batched_plan(ctypes.byref(self._h), self.nmat, arr, _dtype_code(mats[0][2]),
+                                                    self.k, flags, _stream(dev, stream)), "spmv_csr_batched_plan")
+        else:
+            # per-matrix configurations (dicts or gbs_config; None / variant 0 = the library's choice)
+            if len(configs) != self.nmat:
+                raise ValueError("configs must have one entry per matrix")
+            cfgs = (gbs_config * self.nmat)()
+            for b, c in enumerate(configs):
+                if c is not None:
+                    cfgs[b] = _config(c)
+            _capi.check(lib().spmv_csr_batched_plan_cfg(ctypes.byref(self._h), self.nmat, arr,
+                                                        _dtype_code(mats[0][2]), self.k, flags, cfgs,
+                                                        _stream(dev, stream)), "spmv_csr_batched_plan_cfg")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -134,6 +134,8 @@ class gbs_batch_item(ctypes.Structure):
 
 SIGNATURES.update({
     "spmv_csr_batched_plan": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(gbs_batch_item), I32, I32, I32, P]),
+    "spmv_csr_batched_plan_cfg": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(gbs_batch_item), I32, I32, I32,
+                                        ctypes.POINTER(gbs_config), P]),
     "spmv_csr_batched": (I32, [P, P, P, P]),
     "spmv_csr_batched_looped": (I32, [P, P]),
     "spmv_csr_batched_info": (I32, [P, ctypes.POINTER(gbs_config), ctypes.POINTER(I32), ctypes.POINTER(I32),

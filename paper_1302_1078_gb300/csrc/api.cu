@@ -1176,6 +1176,7 @@ struct gbs_batch_plan {
   int G = 1;
   std::vector<gbs_batch_item> items;
   std::vector<gbs_config> cfgs;
+  std::vector<gbs_stats> stats;  // row statistics of each matrix
   std::vector<int> item_begin;  // nmat + 1
   std::vector<MergeBuffers> mbs;
   std::vector<unsigned char> h_desc;
@@ -1270,6 +1271,7 @@ std::vector<gbs_config> batch_candidates(const gbs_stats& st, int dtype, int k) 
   } else {
     add(GBS_VARIANT_ROWS, 0, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile / 2, 0);
+    add(GBS_VARIANT_ROWS, 0, base_tile * 2, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 15);
   }
@@ -1290,6 +1292,64 @@ extern "C" {
 
 int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* items, int dtype, int k, int flags,
                           void* stream) {
+  int rc = spmv_csr_batched_plan_cfg(out, nmat, items, dtype, k, flags, nullptr, stream);
+  if (rc || !(flags & GBS_PLAN_TUNE) || !*out || !(*out)->exec) return rc;
+  // Standalone timings of a small matrix measure its launch latency, not what its items cost
+  // inside a full batch.  So a few whole-batch policies are also built and timed on the
+  // batched kernel itself, and the fastest plan is kept (the per-matrix choice is one of them):
+  //   1: the statistics' variant (ROWS, or MERGE for skewed rows), ROWS with twice the tile;
+  //   2: the per-matrix choice, but MERGE for matrices of short rows (mean < 12);
+  //   3: policy 1, with MERGE for short rows.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  gbs_batch_plan* best = *out;
+  auto time_plan = [&](gbs_batch_plan* q) {
+    return time_median([&] { return cudaGraphLaunch(q->exec, s) == cudaSuccess; }, s);
+  };
+  float best_ms = time_plan(best);
+  if (best_ms < 0) best_ms = 1e30f;
+  const std::vector<gbs_config> tuned = best->cfgs;
+  const std::vector<gbs_stats> stats = best->stats;
+  const int big_tile = dtype == GBS_F64 ? 4096 : 6144;
+  for (int pol = 1; pol <= 3; ++pol) {
+    std::vector<gbs_config> cf(nmat);
+    for (int b = 0; b < nmat; ++b) {
+      const gbs_stats& st = stats[b];
+      gbs_config c = tuned[b];
+      if (pol != 2) {
+        c = heuristic_config(st, dtype, k);
+        if (c.variant == GBS_VARIANT_ROWS) c.tile_nnz = big_tile;
+        if (c.variant == GBS_VARIANT_MERGE) c.items = 0;
+      }
+      if (pol >= 2 && st.mean_row < 12.0) {
+        c = gbs_config{};
+        c.variant = GBS_VARIANT_MERGE;
+      }
+      c.threads = kBatchThreads;
+      cf[b] = c;
+    }
+    gbs_batch_plan* q = nullptr;
+    if (spmv_csr_batched_plan_cfg(&q, nmat, items, dtype, k, flags & ~GBS_PLAN_TUNE, cf.data(), stream) != GBS_OK ||
+        !q || !q->exec) {
+      if (q) batch_free(q);
+      continue;
+    }
+    const float ms = time_plan(q);
+    if (tune_log()) std::fprintf(stderr, "gbspmv batch policy %d: %.4f ms (best so far %.4f ms)\n", pol, ms, best_ms);
+    if (ms > 0 && ms < best_ms) {
+      batch_free(best);
+      best = q;
+      best_ms = ms;
+    } else {
+      batch_free(q);
+    }
+  }
+  *out = best;
+  g_err.clear();
+  return GBS_OK;
+}
+
+int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_item* items, int dtype, int k,
+                              int flags, const gbs_config* cfgs, void* stream) {
   if (!out) return fail(GBS_EINVAL, "plan is NULL");
   *out = nullptr;
   if (nmat < 1 || !items) return fail(GBS_EINVAL, "nmat must be >= 1 and items non-NULL");
@@ -1325,9 +1385,34 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
   cudaGetDevice(&p->device);
   p->items.assign(items, items + nmat);
   p->cfgs.resize(nmat);
+  p->stats.resize(nmat);
   p->mbs.resize(nmat);
 
-  // ---- per-matrix configuration (heuristic, or timed with standalone launches)
+  // ---- the caller's configurations: ROWS or MERGE, run by the batch's 256-thread CTAs
+  std::vector<gbs_config> given_cfgs;
+  if (cfgs) {
+    given_cfgs.assign(cfgs, cfgs + nmat);
+    for (int b = 0; b < nmat; ++b) {
+      gbs_config& g = given_cfgs[b];
+      if (g.variant == GBS_VARIANT_AUTO) continue;
+      int rc = GBS_OK;
+      if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE) {
+        rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": batched configurations are ROWS or MERGE");
+      } else {
+        g.threads = kBatchThreads;
+        g.emul = 0;
+        if (g.variant == GBS_VARIANT_ROWS && k > 1) g.lanes = p->G;
+        g = normalize(g, dtype);
+        rc = check_cfg(g);
+      }
+      if (rc) {
+        batch_free(p);
+        return rc;
+      }
+    }
+  }
+
+  // ---- per-matrix configuration (given, heuristic, or timed with standalone launches)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   const bool tune = (flags & GBS_PLAN_TUNE) != 0;
   if (tune) {
@@ -1336,7 +1421,7 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
   }
   for (int b = 0; b < nmat; ++b) {
     const gbs_batch_item& it = p->items[b];
-    gbs_stats st;
+    gbs_stats& st = p->stats[b];
     int rc = compute_stats(it.m, it.n, it.nnz, it.row_ptr, &st, s);
     if (rc) {
       batch_free(p);
@@ -1345,7 +1430,9 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
     gbs_config c = heuristic_config(st, dtype, k);
     c.threads = kBatchThreads;
     if (c.variant == GBS_VARIANT_ROWS && k > 1) c.lanes = p->G;
-    if (tune && it.m > 0) {
+    const bool given = !given_cfgs.empty() && given_cfgs[b].variant != GBS_VARIANT_AUTO;
+    if (given) c = given_cfgs[b];
+    if (tune && !given && it.m > 0) {
       float best = 1e30f;
       for (gbs_config cand : batch_candidates(st, dtype, k)) {
         if (k > 1 && cand.variant == GBS_VARIANT_ROWS) cand.lanes = p->G;
@@ -1392,7 +1479,10 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       const int lanes = k == 1 ? c.lanes : p->G;
       const int rpc = kBatchThreads / lanes;
       nitems = (it.m + rpc - 1) / rpc;
-      p->smem = std::max(p->smem, rows_smem_host(dtype, rpc, c.tile_nnz));
+      // the staged tile within the batch kernel's shared-memory budget
+      while (p->cfgs[b].tile_nnz > 256 && rows_smem_host(dtype, rpc, p->cfgs[b].tile_nnz) > kBatchSmemBudget)
+        p->cfgs[b].tile_nnz /= 2;
+      p->smem = std::max(p->smem, rows_smem_host(dtype, rpc, p->cfgs[b].tile_nnz));
     } else {
       MergeGeom G = merge_geom(c, it.m, it.nnz, dtype, k, vec16);
       const int capped = batch_cap_items(dtype, G.g, vec16, G.items);

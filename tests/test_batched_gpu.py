@@ -96,6 +96,39 @@ def test_batched_forced_merge_and_new_operands(gbs):
     check_vs_oracle(host2, Y2, torch.float64)
 
 
+@pytest.mark.parametrize("k,dtype", [(8, torch.float64), (1, torch.float64), (1, torch.float32)],
+                         ids=["k8f64", "k1f64", "k1f32"])
+def test_batched_explicit_configs(gbs, k, dtype):
+    """Caller-given per-matrix configurations (ROWS / MERGE / library's choice): equal to the
+    per-matrix loop bitwise and to the oracle; other variants are refused."""
+    mats, Xs, Ys, host = make_batch(SMALL[:18], k, dtype, seed=9)
+    cycle = [dict(variant=2, items=5), dict(variant=1, lanes=2, tile_nnz=96), None,
+             dict(variant=2, items=63), dict(variant=1, lanes=1, tile_nnz=4096), dict(variant=0)]
+    cfgs = [cycle[b % len(cycle)] for b in range(len(mats))]
+    plan = gbs.BatchedPlan(mats, Xs, Ys, configs=cfgs)
+    info = plan.info()
+    for b, c in enumerate(cfgs):
+        if c is not None and c["variant"] != 0:
+            assert info["configs"][b]["variant"] == c["variant"]
+            if c["variant"] == 1:
+                assert info["configs"][b]["tile_nnz"] == c["tile_nnz"]
+    plan.run()
+    torch.cuda.synchronize()
+    batched = [y.clone() for y in Ys]
+    check_vs_oracle(host, batched, dtype)
+    plan.run_looped()
+    torch.cuda.synchronize()
+    for b in range(len(Ys)):
+        assert torch.equal(Ys[b], batched[b]), f"batched != looped for matrix {b}"
+    with pytest.raises(gbs._capi.GbsError):
+        gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=3), None])
+    with pytest.raises(gbs._capi.GbsError):  # tile below 32 nonzeros
+        gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=1, tile_nnz=16), None])
+    if k == 1:  # lanes per row must be a power of two (k > 1 uses the batch's column lanes)
+        with pytest.raises(gbs._capi.GbsError):
+            gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=1, lanes=3), None])
+
+
 def test_batch_offsets_match_oracle(gbs):
     mats, Xs, Ys, host = make_batch(SMALL[:20], 8, torch.float64)
     plan = gbs.BatchedPlan(mats, Xs, Ys)
