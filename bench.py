@@ -295,6 +295,11 @@ def run_gpu(args, rank, world, local_rank):
     gbs.lib()
 
     mats, ks = workload_matrices(args.workload, rank)
+    if args.only:
+        keep = set(args.only.split(","))
+        mats = [(name, A) for name, A in mats if name in keep]
+        if not mats:
+            raise SystemExit(f"--only {args.only}: no such matrix in the workload")
     # ---- resident inputs and tuned plans
     items = []
     for name, A in mats:
@@ -309,7 +314,11 @@ def run_gpu(args, rank, world, local_rank):
             X = synth.uniform(A.n * k, seed=synth.BASE_SEED + 11 + rank, stream=k)
             Xd = torch.from_numpy(X).to(dev).reshape(A.n, k) if k > 1 else torch.from_numpy(X).to(dev)
             Yd = torch.empty((A.m, k) if k > 1 else (A.m,), dtype=torch.float64, device=dev)
-            plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True, emulate=args.emulate)
+            if args.config:
+                # a fixed configuration for every product (profiling runs): no tuning
+                plan = gbs.Plan(rp, ci, A.n, torch.float64, k, config=json.loads(args.config))
+            else:
+                plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True, emulate=args.emulate)
             items.append(dict(name=name, A=A, k=k, rp=rp, ci=ci, v=v, X=Xd, Y=Yd, plan=plan, cfg=plan.config,
                               bytes=compulsory_bytes(A.m, A.n, A.nnz, k), flops=2.0 * A.nnz * k, ucld=ucld))
     stream = torch.cuda.current_stream(dev)
@@ -676,6 +685,11 @@ def main():
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
+    ap.add_argument("--config", default=None,
+                    help='spmv/spmm: one fixed configuration for every product instead of the tuner\'s, as JSON '
+                         '(e.g. \'{"variant": 3, "lanes": 4, "threads": 128}\'); for profiling runs')
+    ap.add_argument("--only", default=None,
+                    help="spmv/spmm: comma-separated matrix names to keep (e.g. stencil3d_100); for profiling runs")
     ap.add_argument("--batch-size", type=int, default=512,
                     help="batched: matrices per batch (512 is the benchmark configuration; smaller for profiling)")
     ap.add_argument("--emulate", action="store_true",

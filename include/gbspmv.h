@@ -91,7 +91,7 @@ typedef enum {
  *                the others on the FP64 pipe, so both pipes work at once.
  *                Each such product is accurate to about 2^-44 of |a x| and the
  *                sums stay within 3e-13 of sum |a x| per entry; operands
- *                outside [2^-100, 2^101) in magnitude use the FP64 pipe.
+ *                outside [2^-38, 2^39) in magnitude use the FP64 pipe.
  */
 typedef struct {
   int variant;

@@ -12,9 +12,11 @@
 //       - lo is the next 23 bits, made exact by subtracting a power of two
 //         that shares lo's exponent (one FADD);
 //       - |d - (hi + lo)| < 2^-46 |d|;
-//       - valid when the exponent of d lies within [-100, 100] (both floats
-//         normal), or when d is zero; other operands are reported, so the
-//         caller can use the native pipe for them.
+//       - valid when the exponent of d lies within [-38, 38], or when d is
+//         zero; other operands are reported, so the caller can use the native
+//         pipe for them.  The range keeps a product of two valid operands
+//         within [2^-76, 2^78), so the product, its exact low part (about
+//         2^-48 of it) and a sum of 48 such products are all normal floats.
 //   * product: a*x = ah*xh + (ah*xl + al*xh) + O(2^-46 |a x|).  ah*xh is
 //     split exactly into p + e1 with one FFMA (24 x 24 bits fit in 48); the
 //     cross terms are added to e1 with two FFMAs.
@@ -35,13 +37,13 @@
 namespace gbs {
 
 // Split d into hi + lo; returns false if d needs the native pipe (|d| outside
-// [2^-100, 2^101) and not zero, or not finite).
+// [2^-38, 2^39) and not zero, or not finite).
 __device__ __forceinline__ bool split_f64(double d, float& hi, float& lo) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(d));
   const unsigned H = static_cast<unsigned>(bits >> 32), L = static_cast<unsigned>(bits);
   const unsigned e = (H >> 20) & 0x7FFu;
   const bool zero = ((H & 0x7FFFFFFFu) | L) == 0u;
-  const bool ok = (e - (1023u - 100u)) <= 200u;  // unsigned wrap: e in [923, 1123]
+  const bool ok = (e - (1023u - 38u)) <= 76u;  // unsigned wrap: e in [985, 1061]
   // hi: rebias the exponent in place (1023 -> 127), then shift mantissa and exponent up by 3
   const unsigned hb = H - ((1023u - 127u) << 20);
   unsigned fhi = __funnelshift_l(L, hb, 3);
@@ -54,6 +56,30 @@ __device__ __forceinline__ bool split_f64(double d, float& hi, float& lo) {
   hi = (ok && !zero) ? h : 0.0f;
   lo = (ok && !zero) ? l : 0.0f;
   return ok || zero;
+}
+
+// A float widened to double with integer operations only (exact; keeps the FP64 pipe, where
+// GB300 also runs the conversion instruction, free for the products).  Handles zeros and
+// subnormal floats; the accumulator never holds infinities or NaNs (operands are range-checked).
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFFu;
+  unsigned m = u & 0x007FFFFFu;
+  unsigned long long bits;
+  if (e != 0u) {
+    bits = sign | (static_cast<unsigned long long>(e + (1023u - 127u)) << 52) |
+           (static_cast<unsigned long long>(m) << 29);
+  } else if (m == 0u) {
+    bits = sign;
+  } else {
+    // subnormal: m * 2^-149 with the leading one of m at bit p
+    const int p = 31 - __clz(m);
+    m &= ~(1u << p);
+    bits = sign | (static_cast<unsigned long long>(p + (1023 - 149)) << 52) |
+           (static_cast<unsigned long long>(m) << (52 - p));
+  }
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 // Float-float accumulator of products of split doubles.
@@ -74,7 +100,19 @@ struct DFAcc {
     c = __fadd_rn(__fsub_rn(sn, __fsub_rn(s2, b2)), __fsub_rn(cn, b2));
     s = s2;
   }
-  __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
+  // s + c is exact in double (at most 48 significant bits): one FP64 add
+  __device__ __forceinline__ double value() const { return widen_f32(s) + widen_f32(c); }
+  // add another accumulator's pair (the lanes of one row), renormalised like add()
+  __device__ __forceinline__ void merge(const DFAcc& o) {
+    const float sn = __fadd_rn(s, o.s);
+    const float bp = __fsub_rn(sn, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bp)), __fsub_rn(o.s, bp));
+    const float cn = __fadd_rn(c, __fadd_rn(err, o.c));
+    const float s2 = __fadd_rn(sn, cn);
+    const float b2 = __fsub_rn(s2, sn);
+    c = __fadd_rn(__fsub_rn(sn, __fsub_rn(s2, b2)), __fsub_rn(cn, b2));
+    s = s2;
+  }
   __device__ __forceinline__ void reset() {
     s = 0.0f;
     c = 0.0f;

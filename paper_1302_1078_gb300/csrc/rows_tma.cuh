@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
   const T* __restrict__ Xc = a.X + c_lo;
   // row partials of the last two blocks (SpMV with LANES > 1), summed one iteration later
   __shared__ T s_red[SPLIT && LANES > 1 ? 2 * 256 : 1];
+  __shared__ float2 s_redf[SPLIT && LANES > 1 && EMUL > 0 ? 2 * 256 : 1];  // the lanes' float-float pairs
 
   // Wait (bounded) for block j's copy in stage j & 1 and add the arrays' last <= 3 nonzeros
   // with plain loads; returns false on timeout.  The caller's barrier publishes the stage.
@@ -198,6 +199,20 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
         T sum = red[tid * LANES];
 #pragma unroll
         for (int l = 1; l < LANES; ++l) sum += red[tid * LANES + l];
+        if constexpr (EMUL > 0) {
+          const float2* rf = s_redf + (j & 1) * 256;
+          DFAcc e;
+          e.s = rf[tid * LANES].x;
+          e.c = rf[tid * LANES].y;
+#pragma unroll
+          for (int l = 1; l < LANES; ++l) {
+            DFAcc o;
+            o.s = rf[tid * LANES + l].x;
+            o.c = rf[tid * LANES + l].y;
+            e.merge(o);
+          }
+          sum += (T)e.value();
+        }
         st_stream(a.Y + (long long)(bj * rpc + tid) * a.ldy, sum);
       }
     }
@@ -227,12 +242,14 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
       const int rs = rp[g], re = rp[g + 1];
       constexpr int STEP = SPLIT ? LANES : 1;
       int p = rs + (SPLIT ? lane : 0);
-      if constexpr (SPLIT && EMUL == 0) {
+      if constexpr (SPLIT) {
         // SpMV: software-pipelined walk of this lane's nonzeros p, p + STEP, ... < re.  The
         // gathers of group q + 1 are issued before the FMAs of group q wait for theirs, and
         // the last 0..3 nonzeros are gathered together, so a row costs about one round trip
         // to L2 per two groups instead of one per group and one per leftover nonzero.  The
-        // products are added in the same order as a plain walk.
+        // products are added in the same order as a plain walk (with EMUL > 0 the first
+        // EMUL products of every full group go to the float-float accumulator, flushed
+        // into the double one every 16 groups).
         const int cnt = p < re ? (re - p + STEP - 1) / STEP : 0;
         const int full = cnt / kUnroll;
         T va[kUnroll], vb[kUnroll];
@@ -247,26 +264,47 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep(Xc + (long long)c[u] * a.ldx, pol_keep);
         };
+        int egroups = 0;
+        auto fma4 = [&](const T* v, const T* x) {
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            if constexpr (EMUL > 0) {
+              if (u < EMUL) {
+                float ah, al, xh, xl;
+                const bool oka = split_f64((double)v[u], ah, al);
+                const bool okx = split_f64((double)x[u], xh, xl);
+                if (oka && okx)
+                  eacc[0].add(ah, al, xh, xl);
+                else
+                  acc[0].add(v[u], x[u]);  // out of the FP32 range: native pipe
+                continue;
+              }
+            }
+            acc[0].add(v[u], x[u]);
+          }
+          if constexpr (EMUL > 0) {
+            if (++egroups == 16) {
+              egroups = 0;
+              acc[0].add_partial((T)eacc[0].value());
+              eacc[0].reset();
+            }
+          }
+        };
         if (full > 0) {
           fetch(0, va, xa);
           int gi = 1;
           for (; gi + 1 < full; gi += 2) {
             fetch(gi * kUnroll, vb, xb);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
+            fma4(va, xa);
             fetch((gi + 1) * kUnroll, va, xa);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc[0].add(vb[u], xb[u]);
+            fma4(vb, xb);
           }
           if (gi < full) {
             fetch(gi * kUnroll, vb, xb);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc[0].add(vb[u], xb[u]);
+            fma4(va, xa);
+            fma4(vb, xb);
           } else {
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) acc[0].add(va[u], xa[u]);
+            fma4(va, xa);
           }
         }
         const int rem = cnt - full * kUnroll;
@@ -282,6 +320,9 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           for (int u = 0; u < kUnroll - 1; ++u)
             if (u < rem) acc[0].add(vb[u], xb[u]);
         }
+        // one lane per row: fold the float-float partial in now; several lanes: the row's
+        // reduction merges the lanes' pairs in FP32 and converts once per row
+        if constexpr (EMUL > 0 && LANES == 1) acc[0].add_partial((T)eacc[0].value());
       } else if (col_full) {
         int groups = 0;
         for (; p + (kUnroll - 1) * STEP < re; p += kUnroll * STEP) {
@@ -349,6 +390,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
     const int r0 = blk * rpc;
     if constexpr (SPLIT && LANES > 1) {
       s_red[st * 256 + tid] = acc[0].value();
+      if constexpr (EMUL > 0) s_redf[st * 256 + tid] = make_float2(eacc[0].s, eacc[0].c);
     } else if constexpr (SPLIT) {
       if (active) st_stream(a.Y + (long long)(r0 + g) * a.ldy, acc[0].value());
     } else {

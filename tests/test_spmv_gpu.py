@@ -362,8 +362,12 @@ def test_emulated_fp64_extreme_magnitudes(gbs):
     m, n, per = 2000, 3000, 24
     rp = np.arange(0, m * per + 1, per, dtype=np.int32)
     ci = np.sort(rng.integers(0, n, (m, per)), axis=1).astype(np.int32).reshape(-1)
-    vmags = np.array([1.0, 1e-200, 1e200, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5], np.float64)
-    xmags = np.array([1.0, 1e-200, 1e100, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5], np.float64)  # products stay finite
+    # 2^38 and 2^-38 sit at the edges of the FP32-pipe range (products up to 2^76 and down to
+    # 2^-76 on the FP32 pipe); 1e30, 2^39 and 2^-39 are just outside it
+    vmags = np.array([1.0, 1e-200, 1e200, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5, 2.0**38, 2.0**-38, 1e30, 2.0**39,
+                      2.0**-39], np.float64)
+    xmags = np.array([1.0, 1e-200, 1e100, 0.0, 5e-324, 1e-31, 3e38, 1e-45, 7.5, 2.0**38, 2.0**-38, 1e30, 2.0**39,
+                      2.0**-39], np.float64)  # products stay finite
     v = rng.uniform(-1, 1, m * per) * vmags[rng.integers(0, vmags.size, m * per)]
     x = rng.uniform(-1, 1, n) * xmags[rng.integers(0, xmags.size, n)]
     A = synth.CSR(m, n, rp, ci, v)
@@ -371,9 +375,10 @@ def test_emulated_fp64_extreme_magnitudes(gbs):
     d_rp, d_ci, d_v = dev_csr(A)
     plan = gbs.Plan(d_rp, d_ci, n, torch.float64, 1)
     for emul in (0, 1, 2, 3):
-        plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, lanes=1, threads=128, emul=emul))
-        y = plan.spmv(d_v, torch.from_numpy(x).cuda())
-        assert_close(y, y_ref, r, torch.float64, f"extreme magnitudes emul={emul}")
+        for lanes, threads in ((1, 128), (4, 128), (8, 256)):
+            plan.set_config(dict(variant=_capi.VARIANT_ROWS_TMA, lanes=lanes, threads=threads, emul=emul))
+            y = plan.spmv(d_v, torch.from_numpy(x).cuda())
+            assert_close(y, y_ref, r, torch.float64, f"extreme magnitudes emul={emul} lanes={lanes}")
 
 
 def test_tuner_with_emulation(gbs):
