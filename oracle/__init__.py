@@ -20,6 +20,9 @@ Parity status of each entry point (the pins are in ``tests/test_oracle.py``):
 * ``backward``: pinned by central finite differences of the bilinear loss
   <A X, W> and by dense brute force.
 * ``batch_offsets``: pinned by brute-force running sums.
+* ``rcm``, ``permute``: pinned by closed forms (a relabelled path has bandwidth 1, a
+  relabelled N x N grid bandwidth N), components and isolated nodes, the breadth-first
+  structure the ordering must have, and scipy's RCM as an independent bandwidth bound.
 * ``ucld``: pinned by the paper's worked example (Sec. 4.1, row 0 19 20 -> 3/16),
   its two extremes (1/line and 1) and brute force on tiny matrices.
 """
@@ -68,6 +71,10 @@ def _load():
             lib.orc_backward_f32.argtypes = [i32, i32, i32, P, P, P, P, ll, P, ll, P, ll, P, P, P]
             lib.orc_batch_offsets.argtypes = [i32, P, P, P, i32, P, P, P, P, P]
             lib.orc_ucld.argtypes = [i32, P, P, i32, P, P, P]
+            lib.orc_rcm.argtypes = [i32, P, P, P]
+            lib.orc_rcm.restype = i32
+            lib.orc_permute.argtypes = [i32, P, P, P, P, P, P, P]
+            lib.orc_permute.restype = i32
             lib.orc_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -184,3 +191,29 @@ def ucld(m, row_ptr, col_idx, line: int = 8):
     tot, rows = ctypes.c_longlong(), ctypes.c_longlong()
     lib.orc_ucld(int(m), _p(rp), _p(ci), int(line), ctypes.byref(u), ctypes.byref(tot), ctypes.byref(rows))
     return u.value, tot.value, rows.value
+
+
+def rcm(n, row_ptr, col_idx):
+    """Reverse Cuthill-McKee permutation (perm[i] = node placed at i) of the symmetric
+    pattern of A + A^T for a square A (Sec. 4.4; tie-breaking rules in oracle.c)."""
+    lib = _load()
+    rp, ci = _c(row_ptr, np.int32), _c(col_idx, np.int32)
+    perm = np.empty(max(int(n), 0), np.int32)
+    if lib.orc_rcm(int(n), _p(rp), _p(ci), _p(perm)) != 0:
+        raise MemoryError("orc_rcm")
+    return perm
+
+
+def permute(n, row_ptr, col_idx, vals, perm):
+    """B = P A P^T: (row_ptr, col_idx, vals) of B, columns sorted within rows."""
+    lib = _load()
+    rp, ci, p = _c(row_ptr, np.int32), _c(col_idx, np.int32), _c(perm, np.int32)
+    v = None if vals is None else _c(vals, np.float64)
+    brp = np.empty(int(n) + 1, np.int32)
+    bci = np.empty(ci.size, np.int32)
+    bv = None if v is None else np.empty(ci.size, np.float64)
+    rc = lib.orc_permute(int(n), _p(rp), _p(ci), None if v is None else _p(v), _p(p), _p(brp), _p(bci),
+                         None if bv is None else _p(bv))
+    if rc != 0:
+        raise MemoryError("orc_permute")
+    return brp, bci, bv

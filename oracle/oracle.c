@@ -323,6 +323,216 @@ void orc_ucld(int m, const int* rptrs, const int* cids, int line, double* ucld, 
   *nonempty = rows;
 }
 
+/* ------------------------------------------------------------------ RCM */
+
+/*
+ * Reverse Cuthill-McKee ordering (Sec. 4.4 applies it to study SpMV; the
+ * paper used MATLAB's implementation, so the tie-breaking rules here are
+ * this library's own, stated in full).  The graph is the symmetric pattern
+ * of A + A^T of a square A, without self loops or repeated edges; deg(v) is
+ * the number of distinct neighbours of v.  Nodes are compared by
+ * (degree, index).
+ *
+ *   1. Nodes of degree 0 come first, in index order.
+ *   2. Then, while nodes remain: s = the smallest remaining node.  A
+ *      pseudo-peripheral node r is found from s (George & Liu): build the
+ *      BFS level structure from r = s; repeatedly take x = the smallest
+ *      node of its last level and build the structure from x; if x's has
+ *      more levels, r = x and continue, otherwise stop.  Cuthill-McKee then
+ *      numbers r's component breadth first from r: the nodes are taken in
+ *      the order they were numbered, and each appends its not yet numbered
+ *      neighbours, smallest first.
+ *   3. The order is reversed: perm[i] is the node placed at position i.
+ *
+ * Returns 0, or -1 if a scratch allocation fails.
+ */
+static int cmp_deg_idx(const int* deg, int a, int b) {
+  if (deg[a] != deg[b]) return deg[a] < deg[b] ? -1 : 1;
+  return (a > b) - (a < b);
+}
+
+static const int* g_sort_deg; /* comparison context for qsort */
+static int cmp_nodes(const void* a, const void* b) {
+  return cmp_deg_idx(g_sort_deg, *(const int*)a, *(const int*)b);
+}
+
+/* Symmetric pattern of A + A^T (no self loops, no repeats): srp[n+1], scol (malloc'd). */
+static int sym_pattern(int n, const int* rptrs, const int* cids, int** srp_out, int** scol_out) {
+  long long nnz = rptrs[n];
+  int* cnt = (int*)calloc((size_t)n + 1, sizeof(int));
+  int* src = (int*)malloc(sizeof(int) * (size_t)(2 * nnz + 1));
+  int* dst = (int*)malloc(sizeof(int) * (size_t)(2 * nnz + 1));
+  if (!cnt || !src || !dst) { free(cnt); free(src); free(dst); return -1; }
+  long long e = 0;
+  for (int i = 0; i < n; ++i)
+    for (int p = rptrs[i]; p < rptrs[i + 1]; ++p) {
+      const int j = cids[p];
+      if (j == i) continue;
+      src[e] = i; dst[e] = j; ++e;
+      src[e] = j; dst[e] = i; ++e;
+    }
+  /* bucket the directed edges by source, then sort each bucket and drop repeats */
+  for (long long q = 0; q < e; ++q) cnt[src[q] + 1]++;
+  for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  int* fill = (int*)malloc(sizeof(int) * (size_t)n);
+  int* adj = (int*)malloc(sizeof(int) * (size_t)(e + 1));
+  if (!fill || !adj) { free(cnt); free(src); free(dst); free(fill); free(adj); return -1; }
+  memcpy(fill, cnt, sizeof(int) * (size_t)n);
+  for (long long q = 0; q < e; ++q) adj[fill[src[q]]++] = dst[q];
+  free(src); free(dst); free(fill);
+  int* srp = (int*)malloc(sizeof(int) * ((size_t)n + 1));
+  if (!srp) { free(cnt); free(adj); return -1; }
+  int out = 0;
+  srp[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const int b = cnt[i], len = cnt[i + 1] - cnt[i];
+    qsort(adj + b, (size_t)len, sizeof(int), cmp_int);
+    for (int q = 0; q < len; ++q)
+      if (q == 0 || adj[b + q] != adj[b + q - 1]) adj[out++] = adj[b + q];
+    srp[i + 1] = out;
+  }
+  free(cnt);
+  *srp_out = srp;
+  *scol_out = adj;
+  return 0;
+}
+
+/* BFS level structure from r over unnumbered nodes; returns the number of levels and
+   the smallest node of the last level in *last_min.  mark/stamp: visited iff mark[v] == stamp. */
+static int bfs_levels(int r, const int* srp, const int* scol, const int* deg, const int* numbered, int* mark,
+                      int stamp, int* queue, int* last_min) {
+  int head = 0, tail = 0, levels = 0;
+  queue[tail++] = r;
+  mark[r] = stamp;
+  while (head < tail) {
+    const int level_end = tail;
+    int best = -1;
+    for (int q = head; q < level_end; ++q)
+      if (best < 0 || cmp_deg_idx(deg, queue[q], best) < 0) best = queue[q];
+    *last_min = best;
+    levels++;
+    for (; head < level_end; ++head) {
+      const int u = queue[head];
+      for (int p = srp[u]; p < srp[u + 1]; ++p) {
+        const int v = scol[p];
+        if (!numbered[v] && mark[v] != stamp) {
+          mark[v] = stamp;
+          queue[tail++] = v;
+        }
+      }
+    }
+  }
+  return levels;
+}
+
+int orc_rcm(int n, const int* rptrs, const int* cids, int* perm) {
+  int *srp = NULL, *scol = NULL;
+  if (n <= 0) return 0;
+  if (sym_pattern(n, rptrs, cids, &srp, &scol)) return -1;
+  int* deg = (int*)malloc(sizeof(int) * (size_t)n);
+  int* byrank = (int*)malloc(sizeof(int) * (size_t)n);
+  int* numbered = (int*)calloc((size_t)n, sizeof(int));
+  int* mark = (int*)calloc((size_t)n, sizeof(int));
+  int* queue = (int*)malloc(sizeof(int) * (size_t)n);
+  int* order = (int*)malloc(sizeof(int) * (size_t)n);
+  int* nb = (int*)malloc(sizeof(int) * (size_t)n);
+  if (!deg || !byrank || !numbered || !mark || !queue || !order || !nb) {
+    free(srp); free(scol); free(deg); free(byrank); free(numbered); free(mark); free(queue); free(order); free(nb);
+    return -1;
+  }
+  for (int v = 0; v < n; ++v) {
+    deg[v] = srp[v + 1] - srp[v];
+    byrank[v] = v;
+  }
+  g_sort_deg = deg;
+  qsort(byrank, (size_t)n, sizeof(int), cmp_nodes); /* nodes by (degree, index) */
+  int placed = 0, cursor = 0, stamp = 0;
+  while (placed < n) {
+    while (numbered[byrank[cursor]]) ++cursor;
+    const int s = byrank[cursor];
+    if (deg[s] == 0) { /* an isolated node: its own component */
+      numbered[s] = 1;
+      order[placed++] = s;
+      continue;
+    }
+    /* pseudo-peripheral node of s's component */
+    int r = s, last = s;
+    int levels = bfs_levels(r, srp, scol, deg, numbered, mark, ++stamp, queue, &last);
+    for (;;) {
+      int last_x = last;
+      const int x = last;
+      const int lx = bfs_levels(x, srp, scol, deg, numbered, mark, ++stamp, queue, &last_x);
+      if (lx > levels) {
+        r = x;
+        levels = lx;
+        last = last_x;
+      } else {
+        break;
+      }
+    }
+    /* Cuthill-McKee from r: each numbered node appends its unnumbered neighbours, smallest first */
+    int head = placed;
+    numbered[r] = 1;
+    order[placed++] = r;
+    while (head < placed) {
+      const int u = order[head++];
+      int k = 0;
+      for (int p = srp[u]; p < srp[u + 1]; ++p)
+        if (!numbered[scol[p]]) nb[k++] = scol[p];
+      qsort(nb, (size_t)k, sizeof(int), cmp_nodes);
+      for (int q = 0; q < k; ++q) {
+        numbered[nb[q]] = 1;
+        order[placed++] = nb[q];
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) perm[i] = order[n - 1 - i];
+  free(srp); free(scol); free(deg); free(byrank); free(numbered); free(mark); free(queue); free(order); free(nb);
+  return 0;
+}
+
+/*
+ * B = P A P^T for perm (perm[i] = the row / column of A placed at i): row i of B is row
+ * perm[i] of A with every column j renumbered to iperm[j], columns sorted ascending
+ * (a stable sort, so repeated columns keep their order).  Values move with their entries.
+ */
+static const int* g_sort_key;
+static int cmp_by_key(const void* a, const void* b) {
+  const int x = g_sort_key[*(const int*)a], y = g_sort_key[*(const int*)b];
+  if (x != y) return (x > y) - (x < y);
+  return (*(const int*)a > *(const int*)b) - (*(const int*)a < *(const int*)b);
+}
+
+int orc_permute(int n, const int* rptrs, const int* cids, const double* val, const int* perm, int* brp, int* bcol,
+                double* bval) {
+  int* iperm = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!iperm) return -1;
+  for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
+  brp[0] = 0;
+  for (int i = 0; i < n; ++i) brp[i + 1] = brp[i] + (rptrs[perm[i] + 1] - rptrs[perm[i]]);
+  int maxlen = 0;
+  for (int i = 0; i < n; ++i)
+    if (rptrs[i + 1] - rptrs[i] > maxlen) maxlen = rptrs[i + 1] - rptrs[i];
+  int* idx = (int*)malloc(sizeof(int) * (size_t)(maxlen > 0 ? maxlen : 1));
+  int* key = (int*)malloc(sizeof(int) * (size_t)(maxlen > 0 ? maxlen : 1));
+  if (!idx || !key) { free(iperm); free(idx); free(key); return -1; }
+  for (int i = 0; i < n; ++i) {
+    const int a = rptrs[perm[i]], len = rptrs[perm[i] + 1] - a;
+    for (int q = 0; q < len; ++q) {
+      idx[q] = q;
+      key[q] = iperm[cids[a + q]];
+    }
+    g_sort_key = key;
+    qsort(idx, (size_t)len, sizeof(int), cmp_by_key);
+    for (int q = 0; q < len; ++q) {
+      bcol[brp[i] + q] = key[idx[q]];
+      if (val && bval) bval[brp[i] + q] = val[a + idx[q]];
+    }
+  }
+  free(iperm); free(idx); free(key);
+  return 0;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP

@@ -480,6 +480,191 @@ def test_ucld_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new)
     assert caught >= 1, f"no pin caught the planted mistake: {name}"
 
 
+# ------------------------------------------------------------------ RCM
+
+def _csr_from_edges(n, edges):
+    rows = [[] for _ in range(n)]
+    for a, b in edges:
+        rows[a].append(b)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.array([c for r in rows for c in sorted(r)], np.int32)
+    return rp, ci
+
+
+def _bandwidth(n, rp, ci):
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    return int(np.abs(rows - ci).max()) if ci.size else 0
+
+
+def _sym_degrees(n, rp, ci):
+    nb = [set() for _ in range(n)]
+    for i in range(n):
+        for j in ci[rp[i]:rp[i + 1]]:
+            if j != i:
+                nb[i].add(int(j))
+                nb[int(j)].add(i)
+    return nb
+
+
+def _check_cm_structure(n, rp, ci, perm, rcm=None):
+    """The reverse of perm must be a Cuthill-McKee order: isolated nodes first in index order;
+    each component starts at a node and continues breadth first, every later node's parent
+    (its earliest placed neighbour) placed before it, parents in non-decreasing position, and
+    the children of one parent sorted by (degree, index)."""
+    rcm = oracle.rcm if rcm is None else rcm
+    order = list(perm[::-1])
+    assert sorted(order) == list(range(n))
+    nb = _sym_degrees(n, rp, ci)
+    deg = [len(x) for x in nb]
+    pos = {v: i for i, v in enumerate(order)}
+    iso = [v for v in order if deg[v] == 0]
+    assert order[:len(iso)] == sorted(iso)
+    last_parent = -1
+    prev = None
+    for i in range(len(iso), n):
+        v = order[i]
+        earlier = [pos[u] for u in nb[v] if pos[u] < i]
+        if not earlier:  # a component's first node
+            last_parent, prev = -1, None
+            continue
+        par = min(earlier)
+        assert par >= last_parent, "parents out of breadth-first order"
+        if par == last_parent:
+            assert (deg[prev], prev) < (deg[v], v), "children not sorted by (degree, index)"
+        last_parent, prev = par, v
+
+
+def test_rcm_path_has_bandwidth_one():
+    rng = np.random.default_rng(80)
+    for n in (2, 3, 17, 200):
+        lab = rng.permutation(n)
+        rp, ci = _csr_from_edges(n, [(lab[i], lab[i + 1]) for i in range(n - 1)])
+        perm = oracle.rcm(n, rp, ci)
+        brp, bci, _ = oracle.permute(n, rp, ci, None, perm)
+        # A has only one direction of each edge: B's pattern is a relabelled path, bandwidth 1
+        assert _bandwidth(n, brp, bci) == 1
+        _check_cm_structure(n, rp, ci, perm)
+
+
+def test_rcm_grid_has_bandwidth_n():
+    """Cuthill-McKee from a corner of an N x N grid numbers it by anti-diagonals: bandwidth N."""
+    for N in (5, 12, 24):
+        A = synth.stencil2d(N)
+        lab = np.random.default_rng(N).permutation(A.m)
+        brp, bci, _ = oracle.permute(A.m, A.row_ptr, A.col_idx, None, lab)
+        perm = oracle.rcm(A.m, brp, bci)
+        crp, cci, _ = oracle.permute(A.m, brp, bci, None, perm)
+        assert _bandwidth(A.m, crp, cci) == N
+        _check_cm_structure(A.m, brp, bci, perm)
+
+
+def test_rcm_starts_at_a_pseudo_peripheral_node():
+    """A spider: centre 0 with arms of 1, 5 and 3 nodes.  The smallest node of degree 1 is the
+    1-arm's end, but the George-Liu search moves the start to the end of the 5-arm (the far
+    end of a longest path), where the Cuthill-McKee order must begin."""
+    arms = [[1], [2, 3, 4, 5, 6], [7, 8, 9]]
+    edges = []
+    for arm in arms:
+        prev = 0
+        for v in arm:
+            edges.append((prev, v))
+            prev = v
+    n = 10
+    rp, ci = _csr_from_edges(n, edges)
+    perm = oracle.rcm(n, rp, ci)
+    assert perm[-1] == 6
+    _check_cm_structure(n, rp, ci, perm)
+
+
+def test_rcm_components_and_isolated_nodes():
+    rng = np.random.default_rng(81)
+    n = 40
+    edges = [(3, 5), (5, 9), (20, 21), (21, 22), (22, 20), (30, 31), (31, 3)]
+    rp, ci = _csr_from_edges(n, edges)
+    perm = oracle.rcm(n, rp, ci)
+    touched = {a for e in edges for a in e}
+    iso = sorted(set(range(n)) - touched)
+    assert list(perm[-len(iso):]) == iso[::-1]  # reversed: isolated nodes last, descending
+    _check_cm_structure(n, rp, ci, perm)
+    for trial in range(6):
+        A = synth.random_csr(80, 80, 0.04, 300 + trial, sorted_cols=bool(trial % 2), duplicates=True,
+                             empty_rows=0.3)
+        _check_cm_structure(A.m, A.row_ptr, A.col_idx, oracle.rcm(A.m, A.row_ptr, A.col_idx))
+
+
+def test_rcm_bandwidth_against_scipy():
+    """scipy's reverse_cuthill_mckee (its own start and tie rules) as an independent yardstick."""
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    for trial, (side, hbw) in enumerate(((30, 4), (60, 9), (40, 15))):
+        n = side * side
+        A = synth.banded(n, hbw=hbw, per_row=min(hbw, 6), seed=400 + trial)
+        lab = np.random.default_rng(trial).permutation(n)
+        brp, bci, _ = oracle.permute(n, A.row_ptr, A.col_idx, None, lab)
+        M = sp.csr_matrix((np.ones(bci.size), bci, brp), shape=(n, n))
+        S = (M + M.T).tocsr()
+        q = csgraph.reverse_cuthill_mckee(S, symmetric_mode=True)
+        ours = oracle.rcm(n, brp, bci)
+        srp, sci, _ = oracle.permute(n, S.indptr, S.indices, None, ours)
+        qrp, qci, _ = oracle.permute(n, S.indptr, S.indices, None, q)
+        assert _bandwidth(n, srp, sci) <= 1.5 * _bandwidth(n, qrp, qci) + 2
+        assert _bandwidth(n, srp, sci) < _bandwidth(n, *oracle.permute(n, S.indptr, S.indices, None, lab)[:2])
+
+
+def test_permute_brute_force():
+    rng = np.random.default_rng(82)
+    for trial in range(8):
+        A = synth.random_csr(60, 60, 0.08, 500 + trial, sorted_cols=bool(trial % 2), duplicates=bool(trial % 3 == 0),
+                             empty_rows=0.2)
+        perm = rng.permutation(A.m).astype(np.int32)
+        brp, bci, bv = oracle.permute(A.m, A.row_ptr, A.col_idx, A.vals, perm)
+        D = A.to_dense()
+        B = synth.CSR(A.m, A.m, brp, bci, bv).to_dense()
+        assert np.array_equal(B, D[perm][:, perm])
+        for i in range(A.m):
+            assert np.all(np.diff(bci[brp[i]:brp[i + 1]]) >= 0)
+
+
+RCM_MUTATIONS = [
+    ("children by index only", "qsort(nb, (size_t)k, sizeof(int), cmp_nodes);", "qsort(nb, (size_t)k, sizeof(int), cmp_int);"),
+    ("not reversed", "for (int i = 0; i < n; ++i) perm[i] = order[n - 1 - i];", "for (int i = 0; i < n; ++i) perm[i] = order[i];"),
+    ("no pseudo-peripheral search", "if (lx > levels) {", "if (0) {"),
+    ("start by index, not degree", "qsort(byrank, (size_t)n, sizeof(int), cmp_nodes); /* nodes by (degree, index) */",
+     "; /* nodes by index */"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", RCM_MUTATIONS, ids=[m[0] for m in RCM_MUTATIONS])
+def test_rcm_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert old in src
+    c = tmp_path / "mut.c"
+    c.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.orc_rcm.argtypes = [i32, P, P, P]
+
+    def mutant(n, rp, ci):
+        rp = np.ascontiguousarray(rp, np.int32)
+        ci = np.ascontiguousarray(ci, np.int32)
+        perm = np.empty(n, np.int32)
+        lib.orc_rcm(int(n), rp.ctypes.data, ci.ctypes.data if ci.size else 0, perm.ctypes.data)
+        return perm
+
+    monkeypatch.setattr(oracle, "rcm", mutant)
+    caught = 0
+    for check in (test_rcm_path_has_bandwidth_one, test_rcm_grid_has_bandwidth_n,
+                  test_rcm_starts_at_a_pseudo_peripheral_node, test_rcm_components_and_isolated_nodes):
+        try:
+            check()
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, f"no pin caught the planted mistake: {name}"
+
+
 # ---------------------------------------------- planted mistakes (mutation)
 
 MUTATIONS = [
