@@ -163,6 +163,37 @@ int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream
 int gbs_ucld(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int line_elems, double* ucld,
              long long* lines, long long* nonempty_rows, void* stream);
 
+/* ------------------------------------------------------------ reordering */
+/*
+ * Reverse Cuthill-McKee ordering (Sec. 4.4 studies its effect on SpMV) of
+ * the symmetric pattern of A + A^T of a square A (n x n), without self loops
+ * or repeated edges.  Nodes are compared by (degree, index): nodes of degree
+ * 0 come first in index order; then, while nodes remain, the smallest
+ * remaining node s is moved to a pseudo-peripheral node r of its component
+ * (George & Liu: from the BFS level structure of r, take the smallest node x
+ * of the last level, and move r to x while x's structure has more levels),
+ * and the component is numbered breadth first from r, each node appending
+ * its unnumbered neighbours smallest first; the order is then reversed.
+ * perm (device, n ints) receives the node placed at each position.
+ * Runs on the device (level-synchronous, exactly the sequential order);
+ * allocates scratch (about 9 ints per row and 7 per nonzero of A) with the
+ * stream-ordered allocator and synchronises `stream`.
+ * Errors: GBS_EINVAL, GBS_EUNSUPPORTED (nnz > 2^30), GBS_ECUDA.
+ */
+int gbs_rcm(int n, int nnz, const int* row_ptr, const int* col_idx, int* perm, void* stream);
+/*
+ * B = P A P^T for a permutation perm of 0..n-1 (perm[i] = the row / column of
+ * A placed at i): row i of B is row perm[i] of A, every column j renumbered
+ * to i' with perm[i'] = j, columns sorted within the row (stably, so repeated
+ * columns keep their order), values (`dtype`) moving with their entries.
+ * Caller buffers (device): b_row_ptr[n+1], b_col_idx[nnz], b_vals[nnz] (vals
+ * and b_vals both NULL for the pattern only).  perm is not checked to be a
+ * permutation.  Asynchronous on `stream` (scratch from the stream-ordered
+ * allocator).
+ */
+int gbs_permute_csr(int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                    const int* perm, int* b_row_ptr, int* b_col_idx, void* b_vals, void* stream);
+
 /* ------------------------------------------------------------------ SpMV */
 /*
  * y <- A x  (Sec. 3).  vals, x and y have type `dtype`; x has n entries and

@@ -155,6 +155,32 @@ def ucld(row_ptr, col_idx, n: int, line_elems: int = 8, stream=None) -> dict:
     return {"ucld": u.value, "lines": tot.value, "nonempty_rows": rows.value}
 
 
+def rcm(row_ptr, col_idx, stream=None):
+    """Reverse Cuthill-McKee permutation (int32 device tensor, perm[i] = node placed at i) of the
+    symmetric pattern of the square matrix (row_ptr, col_idx) (Sec. 4.4), computed on the device."""
+    _check_index(row_ptr, col_idx)
+    dev = _need_cuda(row_ptr, col_idx)
+    n = row_ptr.numel() - 1
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    _capi.check(lib().gbs_rcm(n, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(perm), _stream(dev, stream)),
+                "gbs_rcm")
+    return perm
+
+
+def permute_csr(row_ptr, col_idx, vals, perm, stream=None):
+    """B = P A P^T: (row_ptr, col_idx, vals) of B with columns sorted in every row; vals may be None."""
+    _check_index(row_ptr, col_idx)
+    dev = _need_cuda(row_ptr, col_idx, perm, vals)
+    n, nnz = row_ptr.numel() - 1, col_idx.numel()
+    brp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    bci = torch.empty(nnz, dtype=torch.int32, device=dev)
+    bv = None if vals is None else torch.empty_like(vals)
+    dt = 0 if vals is None else _dtype_code(vals)
+    _capi.check(lib().gbs_permute_csr(n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), dt, _ptr(perm), _ptr(brp),
+                                      _ptr(bci), _ptr(bv), _stream(dev, stream)), "gbs_permute_csr")
+    return brp, bci, bv
+
+
 def validate_csr(row_ptr, col_idx, n: int, stream=None) -> None:
     """Raise GbsError(GBS_EINDEX) if the CSR structure is malformed."""
     dev = _need_cuda(row_ptr, col_idx)

@@ -3,6 +3,7 @@
 // validation.  Every product runs in the kernels of rows_kernel.cuh and
 // merge_kernel.cuh; nothing here computes on the host.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -507,6 +508,33 @@ int gbs_ucld(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int 
   if (lines) *lines = (long long)h[1];
   if (nonempty_rows) *nonempty_rows = (long long)h[2];
   return GBS_OK;
+}
+
+int gbs_rcm(int n, int nnz, const int* row_ptr, const int* col_idx, int* perm, void* stream) {
+  int rc = check_csr(n, n, nnz, row_ptr, col_idx, reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  if (n > 0 && !perm) return fail(GBS_EINVAL, "perm is NULL");
+  if (nnz > INT_MAX / 2) return fail(GBS_EUNSUPPORTED, "nnz above 2^30: the symmetric pattern would not fit int32");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (checked_mode()) {
+    rc = gbs_validate_csr(n, n, nnz, row_ptr, col_idx, stream);
+    if (rc) return rc;
+  }
+  cudaError_t e = rcm_run(n, nnz, row_ptr, col_idx, perm, s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "rcm");
+}
+
+int gbs_permute_csr(int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                    const int* perm, int* b_row_ptr, int* b_col_idx, void* b_vals, void* stream) {
+  int rc = check_csr(n, n, nnz, row_ptr, col_idx, reinterpret_cast<const void*>(1));
+  if (rc) return rc;
+  if (vals && !valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  if (n > 0 && (!perm || !b_row_ptr)) return fail(GBS_EINVAL, "perm or b_row_ptr is NULL");
+  if (nnz > 0 && !b_col_idx) return fail(GBS_EINVAL, "b_col_idx is NULL");
+  if (nnz > 0 && (vals != nullptr) != (b_vals != nullptr)) return fail(GBS_EINVAL, "vals and b_vals: both or neither");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = permute_run(n, nnz, row_ptr, col_idx, vals, dtype, perm, b_row_ptr, b_col_idx, b_vals, s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "permute");
 }
 
 int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out) {

@@ -96,6 +96,13 @@ cudaError_t batched_kernel_call(bool launch, int dtype, bool split, int G, bool 
 cudaError_t launch_ucld(const int* row_ptr, const int* col_idx, int m, int line, unsigned long long* acc,
                         cudaStream_t s);
 
+// Reverse Cuthill-McKee permutation of the symmetric pattern of a square A (rcm.cu;
+// allocates its scratch stream-ordered and synchronises s), and B = P A P^T (vals and
+// bvals may be NULL for the pattern only).
+cudaError_t rcm_run(int n, int nnz, const int* row_ptr, const int* col_idx, int* perm, cudaStream_t s);
+cudaError_t permute_run(int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                        const int* perm, int* brp, int* bcol, void* bvals, cudaStream_t s);
+
 // Message returned by gbs_last_error() on the calling thread (api.cu).
 void set_last_error(const char* msg);
 
