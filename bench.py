@@ -51,11 +51,11 @@ def workload_matrices(name: str, rank: int):
     s = synth.BASE_SEED + 1 + 1000 * rank
     if name == "small":
         return [("stencil2d_64", synth.stencil2d(64))], [1]
-    if name in ("spmv", "spmm"):
+    if name in ("spmv", "spmm", "rcm"):
         mats = [("stencil3d_100", synth.stencil3d(100)),
                 ("banded_2M_hbw1000_50", synth.banded(2_000_000, hbw=1000, per_row=50, seed=s)),
                 ("rmat_s22_ef16", synth.rmat(22, ef=16, seed=s))]
-        return mats, ([1] if name == "spmv" else [1, 4, 8, 16])
+        return mats, ([1, 4, 8, 16] if name == "spmm" else [1])
     raise ValueError(name)
 
 
@@ -69,6 +69,9 @@ WORKLOAD_TEXT = {
     "batched": "Batched FP64 SpMM, 512 CSR matrices (rows log-uniform 1k-200k, avg nnz/row 4-64, round-robin "
                "2D stencil / random banded / R-MAT), k=8 right-hand sides uniform[-1,1], one persistent launch "
                "replayed from a CUDA graph, per-matrix autotuned configuration",
+    "rcm": "FP64 CSR SpMV on the sweep's three matrices before and after reverse Cuthill-McKee reordering "
+           "B = P A P^T computed on the GPU (Sec. 4.4): time of the ordering and of the permutation, SpMV "
+           "GFLOP/s, UCLD (32-byte sectors) and bandwidth max|i-j| of A and B",
     "autograd": "Differentiable SpMV/SpMM on R-MAT scale 20 ef 16, vals uniform[0.5,1.5], k in {1,8}, FP64 and "
                 "FP32: forward Y=A X, backward dX=A^T dY and dvals (transpose built once, timed separately)",
 }
@@ -637,6 +640,80 @@ def run_batched(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ reordering
+
+def run_rcm(args, rank, world, local_rank):
+    import torch
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    mats, _ = workload_matrices("spmv", rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_ms(fn, steps):
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+    def bandwidth(rp, ci):
+        rows = torch.repeat_interleave(torch.arange(rp.numel() - 1, device=dev, dtype=torch.int64),
+                                       (rp[1:] - rp[:-1]).long())
+        return int((rows - ci.long()).abs().max().item()) if ci.numel() else 0
+
+    def measure(rp, ci, v, n):
+        x = torch.from_numpy(synth.uniform(n, seed=synth.BASE_SEED + 11)).to(dev)
+        y = torch.empty(rp.numel() - 1, dtype=torch.float64, device=dev)
+        plan = gbs.Plan(rp, ci, n, torch.float64, 1, tune=True)
+        for _ in range(args.warmup):
+            plan.spmv(v, x, y)
+        ms = timed_ms(lambda: plan.spmv(v, x, y), args.steps)
+        return {"ms": ms, "gflops": 2.0 * ci.numel() / ms / 1e6, "config": plan.config,
+                "ucld_sector_4": gbs.ucld(rp, ci, n, 4)["ucld"], "bandwidth": bandwidth(rp, ci)}
+
+    per, flops, t_before, t_after = [], 0.0, 0.0, 0.0
+    for name, A in mats:
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col_idx).to(dev)
+        v = torch.from_numpy(A.vals).to(dev)
+        before = measure(rp, ci, v, A.n)
+        gbs.rcm(rp, ci)  # warm-up (allocator, module load)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        perm = gbs.rcm(rp, ci)
+        e1.record(stream)
+        brp, bci, bv = gbs.permute_csr(rp, ci, v, perm)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        after = measure(brp, bci, bv, A.n)
+        per.append({"matrix": name, "m": A.m, "nnz": A.nnz, "rcm_ms": e0.elapsed_time(e1),
+                    "permute_ms": e1.elapsed_time(e2), "before": before, "after": after,
+                    "speedup": before["ms"] / after["ms"]})
+        flops += 2.0 * A.nnz
+        t_before += before["ms"]
+        t_after += after["ms"]
+        del rp, ci, v, brp, bci, bv, perm
+    line = {
+        "metric": METRIC, "value": flops / (t_after * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_after, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["rcm"], "l2": "256 MiB write before every product (untimed)"},
+        "value_before_reordering": flops / (t_before * 1e-3) / 1e9, "rcm": per,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ autograd
 
 def run_autograd(args, rank, world, local_rank):
@@ -705,7 +782,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd"])
+    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd", "rcm"])
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
@@ -733,6 +810,8 @@ def main():
         return run_batched(args, rank, world, local_rank)
     if args.workload == "autograd":
         return run_autograd(args, rank, world, local_rank)
+    if args.workload == "rcm":
+        return run_rcm(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
