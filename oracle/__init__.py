@@ -23,6 +23,8 @@ Parity status of each entry point (the pins are in ``tests/test_oracle.py``):
 * ``rcm``, ``permute``: pinned by closed forms (a relabelled path has bandwidth 1, a
   relabelled N x N grid bandwidth N), components and isolated nodes, the breadth-first
   structure the ordering must have, and scipy's RCM as an independent bandwidth bound.
+* ``bcsr``, ``bcsr_spmv``: pinned by dense brute force (the blocks expand back to A),
+  closed-form block counts (identity, dense, block-diagonal) and the fill of a dense block.
 * ``ucld``: pinned by the paper's worked example (Sec. 4.1, row 0 19 20 -> 3/16),
   its two extremes (1/line and 1) and brute force on tiny matrices.
 """
@@ -75,6 +77,9 @@ def _load():
             lib.orc_rcm.restype = i32
             lib.orc_permute.argtypes = [i32, P, P, P, P, P, P, P]
             lib.orc_permute.restype = i32
+            lib.orc_bcsr.argtypes = [i32, i32, P, P, P, i32, i32, P, P, P]
+            lib.orc_bcsr.restype = ll
+            lib.orc_bcsr_spmv.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P]
             lib.orc_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -217,3 +222,27 @@ def permute(n, row_ptr, col_idx, vals, perm):
     if rc != 0:
         raise MemoryError("orc_permute")
     return brp, bci, bv
+
+
+def bcsr(m, n, row_ptr, col_idx, vals, a: int, b: int):
+    """Register-blocked CRS (Sec. 4.5) with aligned a x b dense blocks: (bptr, bcol, bval)."""
+    lib = _load()
+    rp, ci, v = _c(row_ptr, np.int32), _c(col_idx, np.int32), _c(vals, np.float64)
+    mb = (int(m) + a - 1) // a
+    nb = lib.orc_bcsr(int(m), int(n), _p(rp), _p(ci), _p(v), int(a), int(b), None, None, None)
+    if nb < 0:
+        raise MemoryError("orc_bcsr")
+    bptr = np.empty(mb + 1, np.int32)
+    bcol = np.empty(nb, np.int32)
+    bval = np.empty(nb * a * b, np.float64)
+    lib.orc_bcsr(int(m), int(n), _p(rp), _p(ci), _p(v), int(a), int(b), _p(bptr), _p(bcol), _p(bval))
+    return bptr, bcol, bval
+
+
+def bcsr_spmv(m, n, a, b, bptr, bcol, bval, x):
+    """y <- A x from the blocks, with the sums of |products|."""
+    lib = _load()
+    bptr, bcol, bval, x = _c(bptr, np.int32), _c(bcol, np.int32), _c(bval, np.float64), _c(x, np.float64)
+    y, r = np.empty(int(m)), np.empty(int(m))
+    lib.orc_bcsr_spmv(int(m), int(n), int(a), int(b), _p(bptr), _p(bcol), _p(bval), _p(x), _p(y), _p(r))
+    return y, r

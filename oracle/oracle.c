@@ -533,6 +533,81 @@ int orc_permute(int n, const int* rptrs, const int* cids, const double* val, con
   return 0;
 }
 
+/* ----------------------------------------------------------------- BCSR */
+
+/*
+ * Register blocking (Sec. 4.5): A is cut into aligned a x b regions (block
+ * row I = rows I*a .. I*a+a-1, block column J = columns J*b .. J*b+b-1); every
+ * region holding at least one stored entry becomes a dense block, zeros
+ * included, and the list of blocks is stored as CRS over the ceil(m/a) block
+ * rows: bptr[mb+1], bcol[nblocks] (block columns ascending within a block
+ * row), bval[nblocks * a * b] with each block's values row major.  Repeated
+ * entries add up, in storage order.  The first call with bcol == NULL only
+ * returns the block count.
+ */
+long long orc_bcsr(int m, int n, const int* rptrs, const int* cids, const double* val, int a, int b, int* bptr,
+                   int* bcol, double* bval) {
+  const int mb = (m + a - 1) / a;
+  int maxlen = 0;
+  for (int I = 0; I < mb; ++I) {
+    const int r1 = (I + 1) * a < m ? (I + 1) * a : m;
+    const int len = rptrs[r1] - rptrs[I * a];
+    if (len > maxlen) maxlen = len;
+  }
+  int* buf = (int*)malloc(sizeof(int) * (size_t)(maxlen > 0 ? maxlen : 1));
+  if (!buf) return -1;
+  long long nblocks = 0;
+  if (bptr) bptr[0] = 0;
+  for (int I = 0; I < mb; ++I) {
+    const int r0 = I * a, r1 = (I + 1) * a < m ? (I + 1) * a : m;
+    const int p0 = rptrs[r0], len = rptrs[r1] - p0;
+    for (int q = 0; q < len; ++q) buf[q] = cids[p0 + q] / b;
+    qsort(buf, (size_t)len, sizeof(int), cmp_int);
+    const long long first = nblocks;
+    for (int q = 0; q < len; ++q)
+      if (q == 0 || buf[q] != buf[q - 1]) {
+        if (bcol) bcol[nblocks] = buf[q];
+        ++nblocks;
+      }
+    if (bptr) bptr[I + 1] = (int)nblocks;
+    if (bcol && bval) {
+      const long long nbI = nblocks - first;
+      for (long long k = first * a * b; k < nblocks * a * b; ++k) bval[k] = 0.0;
+      for (int i = r0; i < r1; ++i)
+        for (int p = rptrs[i]; p < rptrs[i + 1]; ++p) {
+          const int J = cids[p] / b;
+          long long k = first;
+          while (k < first + nbI && bcol[k] != J) ++k; /* the block of (i, J) */
+          bval[k * a * b + (long long)(i - r0) * b + (cids[p] - J * b)] += val[p];
+        }
+    }
+  }
+  free(buf);
+  (void)n;
+  return nblocks;
+}
+
+/* y <- A x from the blocks: y_i = sum over the blocks of block row i/a of sum_c block[i%a][c] * x[J*b+c]
+   (columns past n do not exist and are skipped), left to right; r = the same sum of |products|. */
+void orc_bcsr_spmv(int m, int n, int a, int b, const int* bptr, const int* bcol, const double* bval,
+                   const double* x, double* y, double* r) {
+  const int mb = (m + a - 1) / a;
+  for (int I = 0; I < mb; ++I)
+    for (int rr = 0; rr < a && I * a + rr < m; ++rr) {
+      double s = 0.0, t = 0.0;
+      for (int k = bptr[I]; k < bptr[I + 1]; ++k)
+        for (int c = 0; c < b; ++c) {
+          const int j = bcol[k] * b + c;
+          if (j >= n) continue;
+          const double pr = bval[(long long)k * a * b + (long long)rr * b + c] * x[j];
+          s = s + pr;
+          t = t + fabs(pr);
+        }
+      y[I * a + rr] = s;
+      if (r) r[I * a + rr] = t;
+    }
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP

@@ -140,6 +140,32 @@ def stencil3d(N: int) -> CSR:
     return CSR(m, m, rp, ci, v, f"stencil3d_{N}")
 
 
+def stencil3d_blocks(N: int, dof: int = 8, seed: int = BASE_SEED + 5) -> CSR:
+    """Block-structured FEM-like matrix: the 27-point stencil on N^3 nodes with ``dof`` unknowns
+    per node, every node-node coupling a dense dof x dof block (rows and columns of node u are
+    u*dof .. u*dof+dof-1).  Off-diagonal values N(0,1), diagonal = sum of |row| + 1.
+    nnz = dof^2 (3N-2)^3.  The register-blocking study's blocky case (aligned blocks fill)."""
+    nodes = stencil3d(N)
+    m = nodes.m * dof
+    deg = np.diff(nodes.row_ptr).astype(np.int64)
+    seg = (nodes.col_idx.astype(np.int64)[:, None] * dof + np.arange(dof)).reshape(-1)  # per node, contiguous
+    row_len = np.repeat(deg * dof, dof)
+    rp = np.zeros(m + 1, np.int64)
+    rp[1:] = np.cumsum(row_len)
+    # row r = u*dof + d takes node u's column segment
+    u_of_row = np.repeat(np.arange(nodes.m), dof)
+    starts = nodes.row_ptr[:-1].astype(np.int64)[u_of_row] * dof
+    lens = row_len
+    idx = np.repeat(starts - rp[:-1], lens) + np.arange(rp[-1])
+    ci = seg[idx].astype(np.int32)
+    v = normal(int(rp[-1]), seed=seed)
+    rows = np.repeat(np.arange(m), lens)
+    diag = ci == rows
+    absum = np.add.reduceat(np.abs(np.where(diag, 0.0, v)), rp[:-1].astype(np.int64)) if m else np.zeros(0)
+    v[diag] = absum + 1.0
+    return CSR(m, m, rp.astype(np.int32), ci, v, f"stencil3d_{N}_dof{dof}")
+
+
 def banded(m: int, hbw: int = 1000, per_row: int = 50, seed: int = BASE_SEED + 1) -> CSR:
     """Random banded FEM-like matrix: |i-j| <= hbw, ``per_row`` distinct columns per row
     (diagonal included), N(0,1) off-diagonals, diagonal = sum |off| + 1."""

@@ -665,6 +665,119 @@ def test_rcm_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new):
     assert caught >= 1, f"no pin caught the planted mistake: {name}"
 
 
+# ----------------------------------------------------------------- BCSR
+
+def _bcsr_dense(m, n, a, b, bptr, bcol, bval):
+    D = np.zeros((((m + a - 1) // a) * a, (max(int(bcol.max()) + 1 if bcol.size else 0, (n + b - 1) // b)) * b))
+    for I in range(bptr.size - 1):
+        for k in range(bptr[I], bptr[I + 1]):
+            D[I * a:(I + 1) * a, bcol[k] * b:(bcol[k] + 1) * b] += bval[k * a * b:(k + 1) * a * b].reshape(a, b)
+    return D
+
+
+BLOCKS = [(8, 1), (1, 8), (2, 8), (4, 8), (8, 4), (8, 2), (8, 8), (3, 5), (1, 1)]
+
+
+def test_bcsr_expands_back_to_a():
+    rng = np.random.default_rng(90)
+    for trial in range(10):
+        m, n = int(rng.integers(1, 70)), int(rng.integers(1, 70))
+        A = synth.random_csr(m, n, float(rng.uniform(0.01, 0.4)), 600 + trial, sorted_cols=bool(trial % 2),
+                             duplicates=bool(trial % 3 == 0), empty_rows=0.2)
+        D = A.to_dense()
+        for a, b in BLOCKS:
+            bptr, bcol, bval = oracle.bcsr(A.m, A.n, A.row_ptr, A.col_idx, A.vals, a, b)
+            E = _bcsr_dense(A.m, A.n, a, b, bptr, bcol, bval)
+            assert np.array_equal(E[:m, :n], D)
+            assert not E[m:, :].any() and not E[:, n:].any()
+            for I in range(bptr.size - 1):  # block columns strictly increasing: no repeated block
+                assert np.all(np.diff(bcol[bptr[I]:bptr[I + 1]]) > 0)
+            # every stored block holds at least one stored entry of A
+            rows = np.repeat(np.arange(A.m), A.row_lengths())
+            keys = set(zip(rows // a, A.col_idx // b))
+            got = {(I, int(bcol[k])) for I in range(bptr.size - 1) for k in range(bptr[I], bptr[I + 1])}
+            assert got == keys
+            x = rng.uniform(-1, 1, A.n)
+            y, r = oracle.bcsr_spmv(A.m, A.n, a, b, bptr, bcol, bval, x)
+            assert np.allclose(y, D @ x, rtol=0, atol=1e-13)
+            assert np.allclose(r, np.abs(E[:m, :n]) @ np.abs(x), rtol=1e-13, atol=1e-15)
+
+
+def test_bcsr_closed_forms():
+    n = 64
+    I = synth.CSR(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    for a, b in BLOCKS:
+        bptr, bcol, _ = oracle.bcsr(n, n, I.row_ptr, I.col_idx, I.vals, a, b)
+        # identity: block (i // a, i // b) for every i, so the blocks are the distinct pairs
+        assert bcol.size == len({(i // a, i // b) for i in range(n)})
+    assert oracle.bcsr(n, n, I.row_ptr, I.col_idx, I.vals, 8, 8)[1].size == 8
+    assert oracle.bcsr(n, n, I.row_ptr, I.col_idx, I.vals, 8, 1)[1].size == n
+    # dense 13 x 21: every region is a block
+    Dn = np.arange(1, 13 * 21 + 1, dtype=np.float64).reshape(13, 21)
+    rp = np.arange(0, 13 * 21 + 1, 21, dtype=np.int32)
+    ci = np.tile(np.arange(21, dtype=np.int32), 13)
+    for a, b in BLOCKS:
+        bptr, bcol, bval = oracle.bcsr(13, 21, rp, ci, Dn.reshape(-1), a, b)
+        assert bcol.size == ((13 + a - 1) // a) * ((21 + b - 1) // b)
+    # the dof-8 block stencil fills 8 x 8 blocks exactly: one block per node coupling
+    N = 4
+    B = synth.stencil3d_blocks(N, 8)
+    bptr, bcol, bval = oracle.bcsr(B.m, B.n, B.row_ptr, B.col_idx, B.vals, 8, 8)
+    assert bcol.size == (3 * N - 2) ** 3 and bval.size == B.nnz and np.all(bval != 0)
+
+
+BCSR_MUTATIONS = [
+    # every replacement stays in bounds
+    ("column mirrored inside the block", "bval[k * a * b + (long long)(i - r0) * b + (cids[p] - J * b)] += val[p];",
+     "bval[k * a * b + (long long)(i - r0) * b + (b - 1 - (cids[p] - J * b))] += val[p];"),
+    ("repeats overwrite", "bval[k * a * b + (long long)(i - r0) * b + (cids[p] - J * b)] += val[p];",
+     "bval[k * a * b + (long long)(i - r0) * b + (cids[p] - J * b)] = val[p];"),
+    ("block columns not made unique", "if (q == 0 || buf[q] != buf[q - 1]) {", "if (1) {"),
+    ("abs bound without abs", "t = t + fabs(pr);", "t = t + pr;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", BCSR_MUTATIONS, ids=[m[0] for m in BCSR_MUTATIONS])
+def test_bcsr_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert old in src
+    c = tmp_path / "mut.c"
+    c.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    lib.orc_bcsr.argtypes = [i32, i32, P, P, P, i32, i32, P, P, P]
+    lib.orc_bcsr.restype = ll
+    lib.orc_bcsr_spmv.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P]
+
+    def bcsr(m, n, rp, ci, v, a, b):
+        rp, ci, v = (np.ascontiguousarray(x, t) for x, t in ((rp, np.int32), (ci, np.int32), (v, np.float64)))
+        nb = lib.orc_bcsr(m, n, rp.ctypes.data, ci.ctypes.data if ci.size else 0, v.ctypes.data if v.size else 0,
+                          a, b, None, None, None)
+        bptr, bcol, bval = np.empty((m + a - 1) // a + 1, np.int32), np.empty(nb, np.int32), np.empty(nb * a * b)
+        lib.orc_bcsr(m, n, rp.ctypes.data, ci.ctypes.data if ci.size else 0, v.ctypes.data if v.size else 0, a, b,
+                     bptr.ctypes.data, bcol.ctypes.data if nb else 0, bval.ctypes.data if nb else 0)
+        return bptr, bcol, bval
+
+    def bcsr_spmv(m, n, a, b, bptr, bcol, bval, x):
+        y, r = np.empty(m), np.empty(m)
+        x = np.ascontiguousarray(x, np.float64)
+        lib.orc_bcsr_spmv(m, n, a, b, bptr.ctypes.data, bcol.ctypes.data if bcol.size else 0,
+                          bval.ctypes.data if bval.size else 0, x.ctypes.data, y.ctypes.data, r.ctypes.data)
+        return y, r
+
+    monkeypatch.setattr(oracle, "bcsr", bcsr)
+    monkeypatch.setattr(oracle, "bcsr_spmv", bcsr_spmv)
+    caught = 0
+    for check in (test_bcsr_expands_back_to_a, test_bcsr_closed_forms):
+        try:
+            check()
+        except (AssertionError, ValueError, IndexError):
+            caught += 1
+    assert caught >= 1, f"no pin caught the planted mistake: {name}"
+
+
 # ---------------------------------------------- planted mistakes (mutation)
 
 MUTATIONS = [
