@@ -194,6 +194,34 @@ int gbs_rcm(int n, int nnz, const int* row_ptr, const int* col_idx, int* perm, v
 int gbs_permute_csr(int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
                     const int* perm, int* b_row_ptr, int* b_col_idx, void* b_vals, void* stream);
 
+/* ------------------------------------------------- register blocking (BCSR) */
+/*
+ * Register-blocked CRS (Sec. 4.5): A (m x n) is cut into aligned a x b
+ * regions (block row I = rows I*a .. I*a+a-1, block column J = columns
+ * J*b .. J*b+b-1, a and b each 1, 2, 4 or 8); every region holding a stored
+ * entry becomes a dense row-major block, zeros included, and the blocks of
+ * a block row are listed by block column, ascending.  Repeated entries add
+ * up in storage order.  The object owns device arrays bptr[ceil(m/a)+1],
+ * bcol[nblocks], bval[nblocks*a*b] (dtype of vals); conversion runs on the
+ * device and synchronises `stream`.  Each block costs a*b multiply-adds in
+ * spmv_bcsr, zeros included, so register blocking pays only where blocks
+ * are dense (the paper: where at least about 70 % of their values are
+ * nonzeros).  x must be finite: a zero of a block times an infinite x is NaN.
+ * Errors: GBS_EINVAL, GBS_EDTYPE, GBS_EUNSUPPORTED (other block sizes),
+ * GBS_ECUDA (including out of memory for sparse blocks).
+ */
+typedef struct gbs_bcsr gbs_bcsr;
+
+int gbs_bcsr_create(gbs_bcsr** plan, int m, int n, int nnz, const int* row_ptr, const int* col_idx,
+                    const void* vals, int dtype, int a, int b, void* stream);
+/* Host copies (any may be NULL): block rows, blocks, a, b. */
+int gbs_bcsr_info(const gbs_bcsr* plan, int* block_rows, long long* nblocks, int* a, int* b);
+/* Device pointers owned by the object (any output may be NULL). */
+int gbs_bcsr_arrays(const gbs_bcsr* plan, const int** bptr, const int** bcol, const void** bval);
+/* y <- A x from the blocks (y: m entries, x: n entries, device, the object's dtype). */
+int spmv_bcsr(const gbs_bcsr* plan, const void* x, void* y, void* stream);
+int gbs_bcsr_destroy(gbs_bcsr* plan);
+
 /* ------------------------------------------------------------------ SpMV */
 /*
  * y <- A x  (Sec. 3).  vals, x and y have type `dtype`; x has n entries and

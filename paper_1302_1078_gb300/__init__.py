@@ -181,6 +181,69 @@ def permute_csr(row_ptr, col_idx, vals, perm, stream=None):
     return brp, bci, bv
 
 
+class BCSR:
+    """Register-blocked CRS (Sec. 4.5) of (row_ptr, col_idx, vals) with aligned a x b dense blocks,
+    converted on the device; spmv(x) multiplies from the blocks."""
+
+    def __init__(self, row_ptr, col_idx, vals, n: int, a: int, b: int, stream=None):
+        _check_index(row_ptr, col_idx)
+        dev = _need_cuda(row_ptr, col_idx, vals)
+        self.m, self.n, self.a, self.b = row_ptr.numel() - 1, int(n), int(a), int(b)
+        self.dtype, self.device = vals.dtype, dev
+        self._h = ctypes.c_void_p()
+        _capi.check(lib().gbs_bcsr_create(ctypes.byref(self._h), self.m, self.n, col_idx.numel(), _ptr(row_ptr),
+                                          _ptr(col_idx), _ptr(vals), _dtype_code(vals), self.a, self.b,
+                                          _stream(dev, stream)), "gbs_bcsr_create")
+        mb, nb = ctypes.c_int(), ctypes.c_longlong()
+        _capi.check(lib().gbs_bcsr_info(self._h, ctypes.byref(mb), ctypes.byref(nb), None, None), "gbs_bcsr_info")
+        self.block_rows, self.nblocks = mb.value, nb.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().gbs_bcsr_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def arrays(self):
+        """Copies of (bptr, bcol, bval) as device tensors."""
+        bp, bc, bv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _capi.check(lib().gbs_bcsr_arrays(self._h, ctypes.byref(bp), ctypes.byref(bc), ctypes.byref(bv)),
+                    "gbs_bcsr_arrays")
+        es = 8 if self.dtype == torch.float64 else 4
+        out = []
+        for ptr, count, dt, size in ((bp, self.block_rows + 1, torch.int32, 4), (bc, self.nblocks, torch.int32, 4),
+                                     (bv, self.nblocks * self.a * self.b, self.dtype, es)):
+            t = torch.empty(count, dtype=dt, device=self.device)
+            if count and ptr.value:
+                torch.cuda.synchronize(self.device)
+                _cudart_copy(t, ptr.value, count * size)
+            out.append(t)
+        return tuple(out)
+
+    def spmv(self, x, y=None, stream=None):
+        _need_cuda(x, y)
+        if y is None:
+            y = torch.empty(self.m, dtype=self.dtype, device=self.device)
+        _capi.check(lib().spmv_bcsr(self._h, _ptr(x), _ptr(y), _stream(self.device, stream)), "spmv_bcsr")
+        return y
+
+
+def _cudart_copy(dst, src_ptr: int, nbytes: int) -> None:
+    """Device-to-device copy from a raw pointer into a tensor (through a zero-copy view)."""
+    import numpy as np  # noqa: F401
+
+    class _Arr:
+        def __init__(self, ptr, n, dt):
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": dt, "data": (ptr, False), "version": 3}
+
+    typestr = {torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4"}[dst.dtype]
+    src = torch.as_tensor(_Arr(src_ptr, dst.numel(), typestr), device=dst.device)
+    dst.copy_(src)
+
+
 def validate_csr(row_ptr, col_idx, n: int, stream=None) -> None:
     """Raise GbsError(GBS_EINDEX) if the CSR structure is malformed."""
     dev = _need_cuda(row_ptr, col_idx)

@@ -86,6 +86,12 @@ SIGNATURES = {
     "gbs_tplan_prepare": (I32, [P, I32, I32, I32, P]),
     "gbs_rcm": (I32, [I32, I32, P, P, P, P]),
     "gbs_permute_csr": (I32, [I32, I32, P, P, P, I32, P, P, P, P, P]),
+    "gbs_bcsr_create": (I32, [ctypes.POINTER(P), I32, I32, I32, P, P, P, I32, I32, I32, P]),
+    "gbs_bcsr_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I32),
+                            ctypes.POINTER(I32)]),
+    "gbs_bcsr_arrays": (I32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),
+    "spmv_bcsr": (I32, [P, P, P, P]),
+    "gbs_bcsr_destroy": (I32, [P]),
     "gbs_ucld": (I32, [I32, I32, I32, P, P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                        ctypes.POINTER(ctypes.c_longlong), P]),
     "gbs_tplan_set_config": (I32, [P, I32, I32, ctypes.POINTER(gbs_config), P]),

@@ -1196,6 +1196,112 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
 
 }  // extern "C"
 
+// ===================================================================== BCSR
+
+struct gbs_bcsr {
+  int m = 0, n = 0, a = 1, b = 1, mb = 0, dtype = GBS_F64, device = 0;
+  long long nblocks = 0;
+  int* bptr = nullptr;
+  int* bcol = nullptr;
+  void* bval = nullptr;
+};
+
+namespace {
+bool block_dim_ok(int d) { return d == 1 || d == 2 || d == 4 || d == 8; }
+void bcsr_free(gbs_bcsr* h) {
+  if (h->bptr) cudaFree(h->bptr);
+  if (h->bcol) cudaFree(h->bcol);
+  if (h->bval) cudaFree(h->bval);
+  delete h;
+}
+}  // namespace
+
+extern "C" {
+
+int gbs_bcsr_create(gbs_bcsr** out, int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
+                    int dtype, int a, int b, void* stream) {
+  if (!out) return fail(GBS_EINVAL, "plan is NULL");
+  *out = nullptr;
+  if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
+  int rc = check_csr(m, n, nnz, row_ptr, col_idx, vals);
+  if (rc) return rc;
+  if (!block_dim_ok(a) || !block_dim_ok(b)) return fail(GBS_EUNSUPPORTED, "block dimensions must be 1, 2, 4 or 8");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (checked_mode()) {
+    rc = gbs_validate_csr(m, n, nnz, row_ptr, col_idx, stream);
+    if (rc) return rc;
+  }
+  gbs_bcsr* h = new (std::nothrow) gbs_bcsr();
+  if (!h) return fail(GBS_ENOMEM, "host allocation");
+  h->m = m;
+  h->n = n;
+  h->a = a;
+  h->b = b;
+  h->mb = (m + a - 1) / a;
+  h->dtype = dtype;
+  cudaGetDevice(&h->device);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->bptr), sizeof(int) * ((size_t)h->mb + 1));
+  if (e != cudaSuccess) {
+    bcsr_free(h);
+    return cuda_fail(e, "cudaMalloc (block row pointers)");
+  }
+  int* sorted = nullptr;
+  void* scratch = nullptr;
+  int nb = 0;
+  e = bcsr_count(m, n, nnz, row_ptr, col_idx, a, b, h->bptr, &sorted, &nb, &scratch, s);
+  if (e == cudaSuccess) {
+    h->nblocks = nb;
+    const size_t vbytes = (size_t)nb * a * b * dsize(dtype);
+    e = cudaMalloc(reinterpret_cast<void**>(&h->bcol), sizeof(int) * (size_t)std::max(nb, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->bval, std::max<size_t>(vbytes, 16));
+    if (e == cudaSuccess)
+      e = bcsr_fill(m, n, nnz, row_ptr, col_idx, vals, dtype, a, b, h->bptr, h->bcol, h->bval, nb, scratch, s);
+  }
+  if (scratch) {
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    bcsr_free(h);
+    return cuda_fail(e, "BCSR conversion");
+  }
+  *out = h;
+  return GBS_OK;
+}
+
+int gbs_bcsr_info(const gbs_bcsr* h, int* block_rows, long long* nblocks, int* a, int* b) {
+  if (!h) return fail(GBS_EINVAL, "plan is NULL");
+  if (block_rows) *block_rows = h->mb;
+  if (nblocks) *nblocks = h->nblocks;
+  if (a) *a = h->a;
+  if (b) *b = h->b;
+  return GBS_OK;
+}
+
+int gbs_bcsr_arrays(const gbs_bcsr* h, const int** bptr, const int** bcol, const void** bval) {
+  if (!h) return fail(GBS_EINVAL, "plan is NULL");
+  if (bptr) *bptr = h->bptr;
+  if (bcol) *bcol = h->bcol;
+  if (bval) *bval = h->bval;
+  return GBS_OK;
+}
+
+int spmv_bcsr(const gbs_bcsr* h, const void* x, void* y, void* stream) {
+  if (!h) return fail(GBS_EINVAL, "plan is NULL");
+  if ((h->m > 0 && !y) || (h->nblocks > 0 && !x)) return fail(GBS_EINVAL, "x or y is NULL");
+  cudaError_t e = bcsr_spmv(h->dtype, h->a, h->b, h->m, h->n, h->bptr, h->bcol, h->bval, x, y,
+                            static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "BCSR SpMV launch");
+}
+
+int gbs_bcsr_destroy(gbs_bcsr* h) {
+  if (h) bcsr_free(h);
+  return GBS_OK;
+}
+
+}  // extern "C"
+
 // ================================================================== batched
 
 struct gbs_batch_plan {

@@ -103,6 +103,17 @@ cudaError_t rcm_run(int n, int nnz, const int* row_ptr, const int* col_idx, int*
 cudaError_t permute_run(int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
                         const int* perm, int* brp, int* bcol, void* bvals, cudaStream_t s);
 
+// Register-blocked CRS (bcsr.cu).  bcsr_count fills bptr[mb+1] and *nblocks (synchronises s)
+// and leaves the sorted block columns in *scratch (stream-ordered allocation) for bcsr_fill,
+// which writes bcol / bval; the caller frees scratch with cudaFreeAsync.
+cudaError_t bcsr_count(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int a, int b, int* bptr,
+                       int** bcol_sorted, int* nblocks, void** scratch, cudaStream_t s);
+cudaError_t bcsr_fill(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
+                      int a, int b, const int* bptr, int* bcol, void* bval, long long nblocks, void* scratch,
+                      cudaStream_t s);
+cudaError_t bcsr_spmv(int dtype, int a, int b, int m, int n, const int* bptr, const int* bcol, const void* bval,
+                      const void* x, void* y, cudaStream_t s);
+
 // Message returned by gbs_last_error() on the calling thread (api.cu).
 void set_last_error(const char* msg);
 
