@@ -51,7 +51,7 @@ def workload_matrices(name: str, rank: int):
     s = synth.BASE_SEED + 1 + 1000 * rank
     if name == "small":
         return [("stencil2d_64", synth.stencil2d(64))], [1]
-    if name in ("spmv", "spmm", "rcm"):
+    if name in ("spmv", "spmm", "rcm", "bcsr"):
         mats = [("stencil3d_100", synth.stencil3d(100)),
                 ("banded_2M_hbw1000_50", synth.banded(2_000_000, hbw=1000, per_row=50, seed=s)),
                 ("rmat_s22_ef16", synth.rmat(22, ef=16, seed=s))]
@@ -72,6 +72,10 @@ WORKLOAD_TEXT = {
     "rcm": "FP64 CSR SpMV on the sweep's three matrices before and after reverse Cuthill-McKee reordering "
            "B = P A P^T computed on the GPU (Sec. 4.4): time of the ordering and of the permutation, SpMV "
            "GFLOP/s, UCLD (32-byte sectors) and bandwidth max|i-j| of A and B",
+    "bcsr": "FP64 SpMV from register-blocked CRS (Sec. 4.5: aligned a x b dense blocks, zeros stored and "
+            "multiplied) against tuned CSR on the sweep's 27-pt 100^3, banded 2M and R-MAT 22 matrices and a "
+            "blocky FEM-like matrix (27-pt stencil on 30^3 nodes with 8 x 8 node couplings, m=216,000, "
+            "nnz=43,614,208); GFLOP/s count only stored entries (2 nnz)",
     "autograd": "Differentiable SpMV/SpMM on R-MAT scale 20 ef 16, vals uniform[0.5,1.5], k in {1,8}, FP64 and "
                 "FP32: forward Y=A X, backward dX=A^T dY and dvals (transpose built once, timed separately)",
 }
@@ -714,6 +718,79 @@ def run_rcm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------ register blocking
+
+def run_bcsr(args, rank, world, local_rank):
+    import torch
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    mats, _ = workload_matrices("spmv", rank)
+    mats = mats + [("stencil3d_30_dof8", synth.stencil3d_blocks(30, 8))]
+    shapes = {"rmat_s22_ef16": [(8, 1), (1, 8)]}  # larger blocks of a power-law matrix are mostly zeros
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+
+    def timed_ms(fn):
+        for _ in range(args.warmup):
+            fn()
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+    per = []
+    for name, A in mats:
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col_idx).to(dev)
+        v = torch.from_numpy(A.vals).to(dev)
+        x = torch.from_numpy(synth.uniform(A.n, seed=synth.BASE_SEED + 11)).to(dev)
+        y = torch.empty(A.m, dtype=torch.float64, device=dev)
+        plan = gbs.Plan(rp, ci, A.n, torch.float64, 1, tune=True)
+        csr_ms = timed_ms(lambda: plan.spmv(v, x, y))
+        entry = {"matrix": name, "m": A.m, "nnz": A.nnz,
+                 "csr": {"ms": csr_ms, "gflops": 2.0 * A.nnz / csr_ms / 1e6, "config": plan.config,
+                         "hbm_frac": compulsory_bytes(A.m, A.n, A.nnz, 1) / csr_ms / 1e6 / hbm_peak}, "bcsr": []}
+        for a, b in shapes.get(name, [(8, 1), (1, 8), (2, 8), (8, 8)]):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B = gbs.BCSR(rp, ci, v, A.n, a, b)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = timed_ms(lambda: B.spmv(x, y))
+            stored = B.nblocks * a * b
+            moved = stored * 8 + B.nblocks * 4 + (B.block_rows + 1) * 4 + 8 * A.n + 8 * A.m
+            entry["bcsr"].append({"a": a, "b": b, "blocks": B.nblocks, "fill": A.nnz / max(stored, 1),
+                                  "convert_ms": e0.elapsed_time(e1), "ms": ms, "gflops": 2.0 * A.nnz / ms / 1e6,
+                                  "relative_to_csr": csr_ms / ms, "block_bytes_hbm_frac": moved / ms / 1e6 / hbm_peak})
+            del B
+        per.append(entry)
+        del rp, ci, v
+    best = sum(min([e["csr"]["ms"]] + [b["ms"] for b in e["bcsr"]]) for e in per)
+    flops = sum(2.0 * e["nnz"] for e in per)
+    line = {
+        "metric": METRIC, "value": flops / (best * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": best, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["bcsr"], "value": "each matrix at its better of CSR and the best block "
+                   "size", "l2": "256 MiB write before every product (untimed)"},
+        "register_blocking": per,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ autograd
 
 def run_autograd(args, rank, world, local_rank):
@@ -782,7 +859,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd", "rcm"])
+    ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd", "rcm", "bcsr"])
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
@@ -812,6 +889,8 @@ def main():
         return run_autograd(args, rank, world, local_rank)
     if args.workload == "rcm":
         return run_rcm(args, rank, world, local_rank)
+    if args.workload == "bcsr":
+        return run_bcsr(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
