@@ -385,9 +385,9 @@ int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, c
  *   - picks each matrix's configuration (ROWS lanes / tile or MERGE items;
  *     256 threads) from its row statistics, or with GBS_PLAN_TUNE by timing
  *     candidates with standalone launches on the given operands (this
- *     writes Y_b), and then by timing a few whole-batch policies on the
- *     batched kernel itself (the statistics' variant with larger ROWS tiles;
- *     MERGE for matrices of short rows), keeping the fastest plan;
+ *     writes Y_b), and then by timing whole-batch policies on the batched
+ *     kernel itself (the statistics' variant with a given ROWS tile, MERGE
+ *     for matrices of short rows, a given merge tile), keeping the fastest;
  *   - builds the work list: matrix b owns the contiguous items
  *     [item_begin[b], item_begin[b+1]) (row blocks or merge tiles); the
  *     grid is every resident CTA slot (`grid`), and each CTA claims the next

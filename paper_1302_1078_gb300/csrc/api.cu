@@ -1429,11 +1429,11 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
   int rc = spmv_csr_batched_plan_cfg(out, nmat, items, dtype, k, flags, nullptr, stream);
   if (rc || !(flags & GBS_PLAN_TUNE) || !*out || !(*out)->exec) return rc;
   // Standalone timings of a small matrix measure its launch latency, not what its items cost
-  // inside a full batch.  So a few whole-batch policies are also built and timed on the
-  // batched kernel itself, and the fastest plan is kept (the per-matrix choice is one of them):
-  //   1: the statistics' variant (ROWS, or MERGE for skewed rows), ROWS with twice the tile;
-  //   2: the per-matrix choice, but MERGE for matrices of short rows (mean < 12);
-  //   3: policy 1, with MERGE for short rows.
+  // inside a full batch.  So whole-batch policies are also built and timed on the batched
+  // kernel itself, and the fastest plan is kept (the per-matrix choice is one of them).  A
+  // policy starts from the per-matrix choice or from the statistics' variant (ROWS with a given
+  // tile, MERGE for skewed rows), and sends matrices whose mean row is shorter than a threshold
+  // to MERGE; MERGE tiles take a given number of items per thread (then capped to the budget).
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   gbs_batch_plan* best = *out;
   auto time_plan = [&](gbs_batch_plan* q) {
@@ -1443,21 +1443,38 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
   if (best_ms < 0) best_ms = 1e30f;
   const std::vector<gbs_config> tuned = best->cfgs;
   const std::vector<gbs_stats> stats = best->stats;
-  const int big_tile = dtype == GBS_F64 ? 4096 : 6144;
-  for (int pol = 1; pol <= 3; ++pol) {
+  const int base_tile = dtype == GBS_F64 ? 2048 : 3072;
+  struct Policy {
+    bool from_stats;  // statistics' variant (else the per-matrix choice)
+    int rows_tile;    // ROWS tile when from_stats
+    double short_row; // mean row below which a matrix takes MERGE (0: none)
+    int merge_items;  // items per merge thread for the MERGE matrices (0: default)
+  };
+  std::vector<Policy> policies;
+  // (merge tiles larger than the default were slower in every policy on the 512-matrix k = 8
+  // batch, so the items dimension stays at the default)
+  for (double thr : {0.0, 8.0, 12.0, 20.0}) {
+    policies.push_back({false, 0, thr, 0});
+    for (int t : {base_tile, 2 * base_tile}) policies.push_back({true, t, thr, 0});
+  }
+  int pol_id = 0;
+  for (const Policy& pol : policies) {
+    ++pol_id;
+    if (!pol.from_stats && pol.short_row == 0.0 && pol.merge_items == 0) continue;  // the per-matrix choice
     std::vector<gbs_config> cf(nmat);
     for (int b = 0; b < nmat; ++b) {
       const gbs_stats& st = stats[b];
       gbs_config c = tuned[b];
-      if (pol != 2) {
+      if (pol.from_stats) {
         c = heuristic_config(st, dtype, k);
-        if (c.variant == GBS_VARIANT_ROWS) c.tile_nnz = big_tile;
-        if (c.variant == GBS_VARIANT_MERGE) c.items = 0;
+        if (c.variant == GBS_VARIANT_ROWS) c.tile_nnz = pol.rows_tile;
       }
-      if (pol >= 2 && st.mean_row < 12.0) {
+      if (pol.short_row > 0.0 && st.mean_row < pol.short_row) {
         c = gbs_config{};
         c.variant = GBS_VARIANT_MERGE;
       }
+      if (c.variant == GBS_VARIANT_MERGE && (pol.from_stats || pol.short_row > 0.0 || pol.merge_items > 0))
+        c.items = pol.merge_items;
       c.threads = kBatchThreads;
       cf[b] = c;
     }
@@ -1468,7 +1485,9 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       continue;
     }
     const float ms = time_plan(q);
-    if (tune_log()) std::fprintf(stderr, "gbspmv batch policy %d: %.4f ms (best so far %.4f ms)\n", pol, ms, best_ms);
+    if (tune_log())
+      std::fprintf(stderr, "gbspmv batch policy %d (stats %d tile %d short<%.0f items %d): %.4f ms (best %.4f ms)\n",
+                   pol_id, (int)pol.from_stats, pol.rows_tile, pol.short_row, pol.merge_items, ms, best_ms);
     if (ms > 0 && ms < best_ms) {
       batch_free(best);
       best = q;
