@@ -66,6 +66,18 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gbs_ucld(4, 4, 0, 16, None, 0, None, None, None, None) == _capi.GBS_EINVAL  # line_elems < 1
     assert lib.gbs_ucld(-1, 4, 0, None, None, 8, None, None, None, None) == _capi.GBS_EINVAL
     assert lib.gbs_tplan_set_config(None, 0, 1, None, None) == _capi.GBS_EINVAL
+    # reordering and register blocking: argument checks on the host
+    assert lib.gbs_rcm(-1, 0, None, None, None, None) == _capi.GBS_EINVAL
+    assert lib.gbs_rcm(4, 0, 16, None, None, None) == _capi.GBS_EINVAL  # perm is NULL
+    assert lib.gbs_permute_csr(4, 0, 16, None, None, 0, None, None, None, None, None) == _capi.GBS_EINVAL
+    assert lib.gbs_permute_csr(4, 0, 16, None, 16, 9, 16, 16, None, 16, None) == _capi.GBS_EDTYPE
+    h = ctypes.c_void_p()
+    assert lib.gbs_bcsr_create(ctypes.byref(h), 4, 4, 0, 16, None, 16, 0, 3, 8, None) == _capi.GBS_EUNSUPPORTED
+    assert lib.gbs_bcsr_create(ctypes.byref(h), 4, 4, 0, 16, None, 16, 7, 8, 8, None) == _capi.GBS_EDTYPE
+    assert lib.gbs_bcsr_create(None, 4, 4, 0, 16, None, 16, 0, 8, 8, None) == _capi.GBS_EINVAL
+    assert lib.spmv_bcsr(None, None, None, None) == _capi.GBS_EINVAL
+    assert lib.gbs_bcsr_destroy(None) == _capi.GBS_OK
+    assert lib.spmv_csr_batched_plan_cfg(None, 1, None, 0, 1, 0, None, None) == _capi.GBS_EINVAL
 
 
 def test_default_config_host_only(lib):
