@@ -75,11 +75,15 @@ __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __r
                                                       int total_items, int* __restrict__ next_item) {
   __shared__ int s_last, s_item;
   int lo = 0;  // matrix of this CTA's previous item
+  // items are claimed one ahead: the claim of the next item is issued when the current one
+  // starts, so the atomic's round trip overlaps the current item's work
+  if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(next_item, 1);
-    __syncthreads();
     const int item = s_item;
     if (item >= total_items) break;
+    int claimed = 0;
+    if (threadIdx.x == 0) claimed = atomicAdd(next_item, 1);
     int hi = nmat - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -120,7 +124,9 @@ __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __r
         if (threadIdx.x == 0) *d.done = 0;
       }
     }
-    __syncthreads();  // shared memory is reused by the next item
+    __syncthreads();  // shared memory is reused by the next item; s_item has been read
+    if (threadIdx.x == 0) s_item = claimed;
+    __syncthreads();
   }
 }
 
