@@ -228,10 +228,21 @@ def cpu_oracle_rate(mats, ks, budget_s: float = 12.0, frac_rows: float | None = 
 
 # --------------------------------------------------------------- reference arm
 
+def reference_matrices(workload: str):
+    """Matrices and k values the reference arm multiplies for a workload: the workload's own
+    matrices, the batch's members (k = 8) or the autograd R-MAT (k = 1 and 8)."""
+    if workload == "batched":
+        specs = synth.batch_specs(512)
+        return [(f"batch_{i}", synth.batch_matrix(sp)) for i, sp in enumerate(specs)], [8]
+    if workload == "autograd":
+        return [("rmat_s20_ef16", synth.rmat(20, ef=16, seed=synth.BASE_SEED + 3, vals="u0.5_1.5"))], [1, 8]
+    return workload_matrices(workload, 0)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    mats, ks = workload_matrices(args.workload, 0)
+    mats, ks = reference_matrices(args.workload)
     import oracle
 
     threads = oracle.max_threads()
