@@ -323,6 +323,51 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
         // one lane per row: fold the float-float partial in now; several lanes: the row's
         // reduction merges the lanes' pairs in FP32 and converts once per row
         if constexpr (EMUL > 0 && LANES == 1) acc[0].add_partial((T)eacc[0].value());
+      } else if (EMUL == 0 && col_full) {
+        // SpMM (the lane owns VEC columns and walks the whole row): the same software
+        // pipeline as the SpMV walk, each gather a VEC-wide slice of an X row
+        const int cnt = re - p;
+        const int full = cnt / kUnroll;
+        T va[kUnroll], vb[kUnroll];
+        Vec<T, VEC> xa[kUnroll], xb[kUnroll];
+        auto fetch = [&](int q0, T* v, Vec<T, VEC>* x) {
+          int c[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            v[u] = sv[p + q0 + u - a0];
+            c[u] = sc[p + q0 + u - a0];
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
+        };
+        auto fma4 = [&](const T* v, const Vec<T, VEC>* x) {
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) acc[j].add(v[u], x[u].v[j]);
+        };
+        if (full > 0) {
+          fetch(0, va, xa);
+          int gi = 1;
+          for (; gi + 1 < full; gi += 2) {
+            fetch(gi * kUnroll, vb, xb);
+            fma4(va, xa);
+            fetch((gi + 1) * kUnroll, va, xa);
+            fma4(vb, xb);
+          }
+          if (gi < full) {
+            fetch(gi * kUnroll, vb, xb);
+            fma4(va, xa);
+            fma4(vb, xb);
+          } else {
+            fma4(va, xa);
+          }
+        }
+        for (int q = full * kUnroll; q < cnt; ++q) {
+          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p + q - a0] * a.ldx, pol_keep);
+#pragma unroll
+          for (int j = 0; j < VEC; ++j) acc[j].add(sv[p + q - a0], xv.v[j]);
+        }
       } else if (col_full) {
         int groups = 0;
         for (; p + (kUnroll - 1) * STEP < re; p += kUnroll * STEP) {
