@@ -719,7 +719,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
             }
         }
     for (int it : {7, 11, 15, 23, 31}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
-    for (int it : {15, 23, 31, 47, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, it);
+    for (int it : {7, 11, 15, 23, 31, 47, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, it);
     for (int it : {31, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 128, 0, it);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
@@ -1338,7 +1338,7 @@ size_t merge_smem_host(int dtype, int g, bool vec16, int items, bool direct) {
   const int nt = kBatchThreads / g;
   const size_t es = dsize(dtype);
   const size_t ipc = (size_t)nt * items;
-  size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
+  size_t a = direct ? 0 : ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
   size_t b = direct ? 0 : ((ipc + 4) * es + 15) & ~(size_t)15;
   size_t c = direct ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
   return a + b + c + 2 * 32 * sizeof(int) + 2 * (size_t)kBatchThreads * vec * es;

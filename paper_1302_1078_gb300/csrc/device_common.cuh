@@ -50,6 +50,14 @@ __device__ __forceinline__ float ld_stream(const float* ptr, uint64_t pol) {
 }
 __device__ __forceinline__ int ld_stream(const int* ptr, uint64_t pol) { return ld_stream_i32(ptr, pol); }
 
+// Four doubles (one whole 32-byte sector) in one 256-bit load that skips L1, leaving L1 to the
+// gathered x and the column sectors; ptr 32-byte aligned.
+__device__ __forceinline__ void ld_stream_4d(const double* ptr, uint64_t pol, double* v) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f64 {%0,%1,%2,%3}, [%4], %5;"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(ptr), "l"(pol));
+}
+
 // ---- streaming loads that do allocate in L1 (for per-thread contiguous segments whose
 //      16-byte loads each use half of a 32-byte sector: the other half then hits L1)
 __device__ __forceinline__ uint4 ld_stream_l1_v4(const void* ptr, uint64_t pol) {
@@ -58,13 +66,6 @@ __device__ __forceinline__ uint4 ld_stream_l1_v4(const void* ptr, uint64_t pol) 
                : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
                : "l"(ptr), "l"(pol));
   return r;
-}
-
-// Four doubles (one 32-byte sector) in one 256-bit load, L1-allocating; ptr 32-byte aligned.
-__device__ __forceinline__ void ld_stream_l1_4d(const double* ptr, uint64_t pol, double* v) {
-  asm volatile("ld.global.nc.L2::cache_hint.v4.f64 {%0,%1,%2,%3}, [%4], %5;"
-               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
-               : "l"(ptr), "l"(pol));
 }
 
 // ---- gathers of the dense operand (reused): L2 evict-last

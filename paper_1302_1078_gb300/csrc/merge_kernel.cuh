@@ -30,9 +30,11 @@
 //     tile's vals / col_idx in shared memory with coalesced loads (MERGE), or
 //     each merge thread reads its own contiguous segment straight from
 //     global memory in aligned 128-bit groups of four (MERGE_DIRECT).  The
-//     direct form needs only the row-pointer window in shared memory (4 bytes
-//     per item instead of 16), which allows more items per thread at the same
-//     residency and spreads the carry scan over more nonzeros.
+//     direct form stages nothing: it reads the tile's row pointers through L1
+//     as well and keeps the next row end in a register, so shared memory holds
+//     only the carry scan's few KB and L1 keeps the rest of the SM's 256 KB
+//     for the gathered x (on a power-law matrix the hot columns of x are what
+//     L1 can hold, and more of them stay there the larger L1 is).
 //   * PERM: the value of stored entry p is vals[perm[p]], so the backward
 //     pass can run A^T on A's values without a permuted copy.  The staged
 //     form gathers the tile's values into shared memory (perm read with
@@ -82,7 +84,7 @@ template <typename T, int VEC, int G, bool DIRECT = false>
 __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
   int nt = threads / G;
   size_t ipc = (size_t)nt * items;
-  size_t a = ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;           // s_rp
+  size_t a = DIRECT ? 0 : ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;  // s_rp
   size_t b = DIRECT ? 0 : ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;  // s_val
   size_t c = DIRECT ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;  // s_col
   size_t d = 2 * 32 * sizeof(int);                                   // s_wkey, s_cinkey
@@ -104,7 +106,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   const int span = (int)((long long)row1 + nz1 - d0);  // items in this tile
 
   int* s_rp = reinterpret_cast<int*>(smem_raw);
-  size_t off = (((size_t)ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
+  size_t off = DIRECT ? 0 : (((size_t)ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
   T* s_val = reinterpret_cast<T*>(smem_raw + off);
   if (!DIRECT) off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
   int* s_col = reinterpret_cast<int*>(smem_raw + off);
@@ -118,19 +120,28 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
 
-  // row_ptr window: s_rp[q] = row_ptr[row0 + q] for rows row0 .. min(row1, m-1), plus its end
-  const int rlast = min(row1, a.m - 1);
-  const int nrp = rlast >= row0 ? rlast - row0 + 2 : 0;
-  for (int q = threadIdx.x; q < nrp; q += blockDim.x) s_rp[q] = ld_stream(a.row_ptr + row0 + q, pol_stream);
+  // row_ptr window rp(q) = row_ptr[row0 + q], q in [0, row1 - row0]: staged in shared memory
+  // (rows row0 .. min(row1, m-1) plus the last one's end), or read through L1 (DIRECT)
   const int a0 = nz0 & ~3;
-  if (!DIRECT && nz1 > nz0) {
-    if constexpr (PERM)
-      stage_gather<T>(s_val, a.vals, a.perm, a0, nz1, a.aligned_vals, pol_stream);
-    else
-      stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
-    stage_copy<int>(s_col, a.col_idx, a0, nz1, a.aligned_cols, pol_stream);
+  if constexpr (!DIRECT) {
+    const int rlast = min(row1, a.m - 1);
+    const int nrp = rlast >= row0 ? rlast - row0 + 2 : 0;
+    for (int q = threadIdx.x; q < nrp; q += blockDim.x) s_rp[q] = ld_stream(a.row_ptr + row0 + q, pol_stream);
+    if (nz1 > nz0) {
+      if constexpr (PERM)
+        stage_gather<T>(s_val, a.vals, a.perm, a0, nz1, a.aligned_vals, pol_stream);
+      else
+        stage_copy<T>(s_val, a.vals, a0, nz1, a.aligned_vals, pol_stream);
+      stage_copy<int>(s_col, a.col_idx, a0, nz1, a.aligned_cols, pol_stream);
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  auto rp = [&](int q) -> int {
+    if constexpr (DIRECT)
+      return __ldg(a.row_ptr + row0 + q);
+    else
+      return s_rp[q];
+  };
 
   const int t = threadIdx.x / G;            // merge thread
   const int lane = threadIdx.x % G;         // column lane inside the merge thread
@@ -142,26 +153,33 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   const bool col_active = c_lo < a.k;
   const bool col_full = c_lo + VEC <= a.k;
 
-  // this merge thread's share of the tile: diagonals [ds, de) relative to d0
+  // this merge thread's share of the tile: diagonals [ds, de) relative to d0, each located by a
+  // binary search of the window; the two searches step together so their reads overlap
   const int ds = min(t * a.items, span), de = min(ds + a.items, span);
   const int wrows = row1 - row0, wnz = nz1 - nz0;
-  auto local_search = [&](int dd) {
-    int lo = max(0, dd - wnz), hi = min(dd, wrows);
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (s_rp[mid + 1] <= nz0 + dd - 1 - mid)
-        lo = mid + 1;
+  int ri_s = max(0, ds - wnz), hi_s = min(ds, wrows);
+  int ri_e = max(0, de - wnz), hi_e = min(de, wrows);
+  while (ri_s < hi_s || ri_e < hi_e) {
+    const int ms = (ri_s + hi_s) >> 1, me = (ri_e + hi_e) >> 1;
+    const int vs = rp(min(ms + 1, wrows)), ve = rp(min(me + 1, wrows));
+    if (ri_s < hi_s) {
+      if (vs <= nz0 + ds - 1 - ms)
+        ri_s = ms + 1;
       else
-        hi = mid;
+        hi_s = ms;
     }
-    return lo;
-  };
-  const int ri_s = local_search(ds), ri_e = local_search(de);
+    if (ri_e < hi_e) {
+      if (ve <= nz0 + de - 1 - me)
+        ri_e = me + 1;
+      else
+        hi_e = me;
+    }
+  }
   const int row_s = row0 + ri_s, nz_s = nz0 + ds - ri_s;
   const int row_e = row0 + ri_e, nz_e = nz0 + de - ri_e;
 
   // the thread's first row started before its first nonzero: earlier threads hold its start
-  const bool head_partial = (row_s < a.m) && (nz_s > s_rp[ri_s]);
+  const bool head_partial = (row_s < a.m) && (nz_s > rp(ri_s));
 
   Acc<T> acc[VEC];
   T head[VEC];
@@ -206,6 +224,15 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       }
       return xv;
     };
+    // end of the current row, row_ptr[row + 1]; past every nonzero once the thread's rows are emitted
+    int rnext = row < row_e ? rp(row - row0 + 1) : 0x7fffffff;
+    auto close_rows = [&](int q) {
+      while (rnext <= q) {
+        emit(row);
+        ++row;
+        rnext = row < row_e ? rp(row - row0 + 1) : 0x7fffffff;
+      }
+    };
     auto one = [&](int q) {
       T vv;
       if constexpr (PERM)
@@ -215,10 +242,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       const int cc = ld_stream(a.col_idx + q, pol_stream);
       Vec<T, VEC> xv;
       if (col_active) xv = gather(cc);
-      while (row < row_e && s_rp[row - row0 + 1] <= q) {
-        emit(row);
-        ++row;
-      }
+      close_rows(q);
       if (col_active) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) acc[j].add(vv, xv.v[j]);
@@ -237,7 +261,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
           v[3] = __ldg(a.vals + (int)pw.w);
         } else if constexpr (sizeof(T) == 8) {
           if (a.vals32) {
-            ld_stream_l1_4d(reinterpret_cast<const double*>(a.vals + nz), pol_stream, reinterpret_cast<double*>(v));
+            ld_stream_4d(reinterpret_cast<const double*>(a.vals + nz), pol_stream, reinterpret_cast<double*>(v));
           } else {
             const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
             const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
@@ -262,10 +286,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          while (row < row_e && s_rp[row - row0 + 1] <= nz + u) {
-            emit(row);
-            ++row;
-          }
+          close_rows(nz + u);
           if (col_active) {
 #pragma unroll
             for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
