@@ -286,7 +286,8 @@ int spmm_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, 
  * A plan fixes the structure (m, n, nnz, row_ptr, col_idx), the dtype and k,
  * computes the row-length statistics, picks a configuration and owns any
  * scratch it needs.  With GBS_PLAN_TUNE it times candidate configurations
- * on the device (on scratch values it allocates itself) and keeps the
+ * on the device (on scratch values it allocates itself, each run after a
+ * write of twice the L2's size so that it starts cold) and keeps the
  * fastest (with GBS_PLAN_EMULATE also candidates that run part of the FP64
  * products on the FP32 pipe).  With GBS_PLAN_CHECK it validates the structure first.  The plan
  * keeps row_ptr and col_idx as given: they must stay valid and unchanged
