@@ -44,6 +44,14 @@
 
 namespace gbs {
 
+// A 32-bit read that may hit L1 (the direct form's row pointers, which its searches re-read),
+// with an L2 policy.
+__device__ __forceinline__ int ld_l1_i32(const int* ptr, uint64_t pol) {
+  int r;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(ptr), "l"(pol));
+  return r;
+}
+
 template <typename T>
 struct MergeArgs {
   int m, k, nnz;
@@ -138,7 +146,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   }
   auto rp = [&](int q) -> int {
     if constexpr (DIRECT)
-      return __ldg(a.row_ptr + row0 + q);
+      return ld_l1_i32(a.row_ptr + row0 + q, pol_stream);
     else
       return s_rp[q];
   };
