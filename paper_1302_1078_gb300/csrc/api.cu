@@ -725,6 +725,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 256, base_tile / 2, 0);
+    add(GBS_VARIANT_ROWS_TMA, 0, 64, 0, 0);
     add(GBS_VARIANT_ROWS_TMA, 0, 128, 0, 0);
     add(GBS_VARIANT_ROWS_TMA, 0, 256, 0, 0);
     if (p->dtype == GBS_F64 && (p->flags & GBS_PLAN_EMULATE))
