@@ -707,7 +707,8 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     }
     add(GBS_VARIANT_ROWS, 1, 128, fit_tile(128, 1), 0);
     add(GBS_VARIANT_ROWS, 2, 128, fit_tile(128, 2), 0);
-    const int tma_shapes[][2] = {{1, 32}, {1, 64}, {1, 128}, {2, 64}, {2, 128}, {2, 256}, {4, 128}, {4, 256}, {8, 256}};
+    const int tma_shapes[][2] = {{1, 32}, {1, 64}, {1, 128}, {2, 64}, {2, 128}, {2, 256}, {4, 96}, {4, 128},
+                                 {4, 160}, {4, 192}, {4, 224}, {4, 256}, {8, 256}};
     for (const auto& sh : tma_shapes)
       for (int l = sh[0], th = sh[1], once = 1; once; once = 0)
         if (l == 1 || p->stats.mean_row >= 0.5 * l) {
@@ -788,9 +789,10 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
       if (check_cfg(c) != GBS_OK) continue;
       p->cfg = c;
       if (plan_prepare(p, s) != GBS_OK) continue;
-      float times[3];
+      constexpr int kReps = 7;  // timed runs after one untimed; the median is kept
+      float times[kReps];
       bool ok = true;
-      for (int r = 0; r < 4 && ok; ++r) {
+      for (int r = 0; r <= kReps && ok; ++r) {
         if (flush && cudaMemsetAsync(flush, r, bf, s) != cudaSuccess) ok = false;
         if (ok && cudaEventRecord(ev0, s) != cudaSuccess) ok = false;
         if (ok && plan_run(p, vals, X, ldx, Y, ldx, s) != GBS_OK) ok = false;
@@ -801,12 +803,12 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
         if (r > 0) times[r - 1] = ms;
       }
       if (!ok) continue;
-      std::sort(times, times + 3);
+      std::sort(times, times + kReps);
       if (tune_log())
         std::fprintf(stderr, "gbspmv tune m=%d nnz=%d k=%d: variant=%d lanes=%d threads=%d tile=%d items=%d emul=%d -> %.4f ms\n",
-                     p->m, p->nnz, p->k, c.variant, c.lanes, c.threads, p->cfg.tile_nnz, c.items, c.emul, times[1]);
-      if (times[1] < best) {
-        best = times[1];
+                     p->m, p->nnz, p->k, c.variant, c.lanes, c.threads, p->cfg.tile_nnz, c.items, c.emul, times[kReps / 2]);
+      if (times[kReps / 2] < best) {
+        best = times[kReps / 2];
         best_cfg = c;
       }
     }

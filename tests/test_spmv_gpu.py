@@ -261,7 +261,8 @@ def test_full_size_spmv_tuned_plan(gbs, name):
 # ------------------------------------------- pipelined ROWS (bulk-copy staging)
 
 TMA_SHAPES = [dict(lanes=1, threads=64), dict(lanes=1, threads=128), dict(lanes=1, threads=256), dict(lanes=2, threads=64),
-              dict(lanes=4, threads=256), dict(lanes=8, threads=128), dict(lanes=32, threads=256)]
+              dict(lanes=4, threads=192), dict(lanes=4, threads=256), dict(lanes=8, threads=128),
+              dict(lanes=32, threads=256)]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
