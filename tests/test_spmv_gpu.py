@@ -258,6 +258,20 @@ def test_full_size_spmv_tuned_plan(gbs, name):
     assert_close(y2, y_ref, r, torch.float64, f"{name} auto")
 
 
+
+@pytest.mark.parametrize("k", [4, 8, 16])
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_spmm_tuned_plan(gbs, name, k):
+    """The SpMM benchmark's matrices, widths and launch path (tuned plan), every entry checked."""
+    A = FULL[name]()
+    X = synth.uniform(A.n * k, seed=synth.BASE_SEED + 2, stream=k).reshape(A.n, k)
+    Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals, X, threads=oracle.max_threads())
+    rp, ci, v = dev_csr(A)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, k, tune=True)
+    Y = torch.full((A.m, k), float("nan"), dtype=torch.float64, device="cuda")
+    plan.spmm(v, torch.from_numpy(X).cuda(), Y)
+    assert_close(Y, Y_ref, R, torch.float64, f"{name} k={k} {plan.config}")
+
 # ------------------------------------------- pipelined ROWS (bulk-copy staging)
 
 TMA_SHAPES = [dict(lanes=1, threads=64), dict(lanes=1, threads=128), dict(lanes=1, threads=256), dict(lanes=2, threads=64),
