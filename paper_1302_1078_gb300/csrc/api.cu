@@ -640,8 +640,10 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
     if (rc) return rc;
     const int tile = ((mx + 8 + 31) / 32) * 32;
     const size_t smem = rows_tma_smem(p->dtype, rpc, tile);
-    // 227 KB per CTA, less the kernel's static shared memory (two blocks of row partials)
-    if (tile > (1 << 14) || smem > 227 * 1024 - 2 * 256 * 8 - 64)
+    // 227 KB per CTA, less the kernel's static shared memory (two blocks of row partials, and
+    // of float-float pairs when emulating)
+    const size_t stat = 2 * 256 * 8 + (p->cfg.emul ? 2 * 256 * 8 : 0) + 64;
+    if (tile > (1 << 14) || smem > 227 * 1024 - stat)
       return fail(GBS_EUNSUPPORTED, "row blocks too large for ROWS_TMA");
     p->cfg.tile_nnz = tile;
     return GBS_OK;
