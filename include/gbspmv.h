@@ -40,6 +40,11 @@
  *   - The library does not check the values of row_ptr or col_idx on the
  *     device unless asked (gbs_validate_csr, or a plan built with
  *     GBS_PLAN_CHECK): malformed indices read out of bounds.
+ *   - Sizes: m + nnz <= 2^31 - 4097 for every entry point that takes a CSR
+ *     matrix (32-bit positions, with headroom for the kernels' rounding of
+ *     nonzero ranges); larger returns GBS_EUNSUPPORTED before any launch.
+ *     Dense operands are addressed with 64-bit offsets (column j of X at
+ *     j * ldx), so n * ldx may exceed 2^31.
  */
 #ifndef GBSPMV_H
 #define GBSPMV_H

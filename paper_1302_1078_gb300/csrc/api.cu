@@ -46,11 +46,15 @@ int pow2ceil(int v) {
 }
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+constexpr long long kMaxRowsPlusNnz = 0x7fffffffLL - 4096;
+
 int check_csr(int m, int n, int nnz, const int* rp, const int* ci, const void* vals) {
   if (m < 0 || n < 0 || nnz < 0) return fail(GBS_EINVAL, "negative size");
   if (m > 0 && rp == nullptr) return fail(GBS_EINVAL, "row_ptr is NULL");
   if (nnz > 0 && (ci == nullptr || vals == nullptr)) return fail(GBS_EINVAL, "col_idx or vals is NULL");
-  if ((long long)m + nnz > 0x7fffffffLL) return fail(GBS_EUNSUPPORTED, "m + nnz must be below 2^31");
+  // 32-bit positions with headroom: the kernels round nonzero ranges out to 4-element groups
+  // and step a few groups past a position before comparing it with the range's end
+  if ((long long)m + nnz > kMaxRowsPlusNnz) return fail(GBS_EUNSUPPORTED, "m + nnz must be at most 2^31 - 4097");
   return GBS_OK;
 }
 
@@ -238,7 +242,7 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
 __global__ void stats_kernel(const int* __restrict__ rp, int m, unsigned long long* __restrict__ acc, int* __restrict__ maxrow) {
   unsigned long long sq = 0, empty = 0, o32 = 0, o256 = 0, o4k = 0;
   int mx = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
     const int len = rp[i + 1] - rp[i];
     sq += (unsigned long long)len * (unsigned long long)len;
     empty += len == 0;
@@ -267,15 +271,15 @@ __global__ void stats_kernel(const int* __restrict__ rp, int m, unsigned long lo
 
 __global__ void validate_kernel(const int* __restrict__ rp, const int* __restrict__ ci, int m, int n, int nnz,
                                 int* __restrict__ flags) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
   int f = 0;
   if (tid == 0) {
     if (rp[0] != 0) f |= 1;
     if (rp[m] != nnz) f |= 2;
   }
-  for (int i = tid; i < m; i += nt)
+  for (long long i = tid; i < m; i += nt)
     if (rp[i + 1] < rp[i]) f |= 4;
-  for (int p = tid; p < nnz; p += nt) {
+  for (long long p = tid; p < nnz; p += nt) {
     const int c = ci[p];
     if (c < 0 || c >= n) f |= 8;
   }
@@ -321,8 +325,8 @@ int compute_stats(int m, int n, int nnz, const int* rp, gbs_stats* out, cudaStre
 __global__ void block_max_nnz_kernel(const int* __restrict__ rp, int m, int rpc, int* __restrict__ out) {
   const int nb = (m + rpc - 1) / rpc;
   int mx = 0;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
-    mx = max(mx, rp[min(m, (b + 1) * rpc)] - rp[b * rpc]);
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (long long)gridDim.x * blockDim.x)
+    mx = max(mx, rp[min((long long)m, (b + 1) * rpc)] - rp[b * rpc]);
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) sddmm_kernel(int nnz, int k, const int* _
                                                     T* __restrict__ dvals) {
   const uint64_t pol_keep = policy_evict_last();
   const uint64_t pol_stream = policy_evict_first();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += gridDim.x * blockDim.x) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) {
     const int i = ld_stream(rows + p, pol_stream);
     const int j = ld_stream(col_idx + p, pol_stream);
     const T* __restrict__ xr = X + (long long)j * ldx;

@@ -37,11 +37,11 @@ int grid_for(long long work) {
 }
 
 __global__ void slice_rows_k(int mb, int a, int m, const int* __restrict__ rp, int* __restrict__ gp) {
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I <= mb; I += gridDim.x * blockDim.x)
-    gp[I] = rp[min(I * a, m)];
+  for (long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x; I <= mb; I += (long long)gridDim.x * blockDim.x)
+    gp[I] = rp[min(I * a, (long long)m)];
 }
 __global__ void block_cols_k(int nnz, int b, const int* __restrict__ ci, int* __restrict__ gc) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += gridDim.x * blockDim.x) gc[p] = ci[p] / b;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) gc[p] = ci[p] / b;
 }
 // distinct sorted values per row: count (FILL == false) or write
 template <bool FILL>
@@ -67,7 +67,7 @@ template <typename T>
 __global__ void scatter_vals_k(int m, int a, int b, const int* __restrict__ rp, const int* __restrict__ ci,
                                const T* __restrict__ vals, const int* __restrict__ bptr, const int* __restrict__ bcol,
                                T* __restrict__ bval) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
     const int I = i / a, r = i - I * a;
     const int lo0 = bptr[I], hi0 = bptr[I + 1];
     for (int p = rp[i]; p < rp[i + 1]; ++p) {

@@ -52,7 +52,7 @@ int grid_for(long long work) {
 int grid_warps(long long warps) { return grid_for(warps * 32); }
 
 __global__ void iota_k(int* __restrict__ out, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) out[i] = i;
 }
 
 // Merge of two sorted lists per row without `i` and repeats: count (fill == false) or write.
@@ -60,7 +60,7 @@ template <bool FILL>
 __global__ void sym_merge_k(int n, const int* __restrict__ rpa, const int* __restrict__ ca, const int* __restrict__ rpb,
                             const int* __restrict__ cb, int* __restrict__ cnt, const int* __restrict__ rps,
                             int* __restrict__ cs) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     int p = rpa[i], pe = rpa[i + 1], q = rpb[i], qe = rpb[i + 1];
     int out = FILL ? rps[i] : 0, k = 0, last = -1;
     while (p < pe || q < qe) {
@@ -79,16 +79,16 @@ __global__ void sym_merge_k(int n, const int* __restrict__ rpa, const int* __res
 }
 
 __global__ void degrees_k(int n, const int* __restrict__ rp, int* __restrict__ deg) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) deg[i] = rp[i + 1] - rp[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) deg[i] = rp[i + 1] - rp[i];
 }
 
 __global__ void rank_of_k(int n, const int* __restrict__ byrank, int* __restrict__ rank) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) rank[byrank[r]] = r;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) rank[byrank[r]] = r;
 }
 
 // rows of S in rank order: length and copy
 __global__ void qlen_k(int n, const int* __restrict__ byrank, const int* __restrict__ deg, int* __restrict__ qlen) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) qlen[r] = deg[byrank[r]];
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) qlen[r] = deg[byrank[r]];
 }
 __global__ void qfill_k(int n, const int* __restrict__ byrank, const int* __restrict__ rps, const int* __restrict__ cs,
                         const int* __restrict__ rpq, int* __restrict__ cq) {
@@ -106,19 +106,19 @@ __global__ void map_k(long long cnt, const int* __restrict__ idx, const int* __r
 }
 
 __global__ void fill_k(int* __restrict__ a, int n, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) a[i] = v;
 }
 
 // isolated nodes: the first `iso` nodes in rank order
 __global__ void place_prefix_k(int iso, const int* __restrict__ byrank, int* __restrict__ order, int* __restrict__ pos) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < iso; r += gridDim.x * blockDim.x) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < iso; r += (long long)gridDim.x * blockDim.x) {
     order[r] = byrank[r];
     pos[byrank[r]] = r;
   }
 }
 __global__ void count_zero_deg_k(int n, const int* __restrict__ deg, int* __restrict__ out) {
   int c = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += deg[i] == 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) c += deg[i] == 0;
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
@@ -126,8 +126,8 @@ __global__ void count_zero_deg_k(int n, const int* __restrict__ deg, int* __rest
 // smallest k in [b, e) whose node byrank[k] is not numbered
 __global__ void find_unnumbered_k(int b, int e, const int* __restrict__ byrank, const int* __restrict__ pos,
                                   int* __restrict__ out) {
-  for (int k = b + blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x)
-    if (pos[byrank[k]] < 0) atomicMin(out, k);
+  for (long long k = b + (long long)blockIdx.x * blockDim.x + threadIdx.x; k < e; k += (long long)gridDim.x * blockDim.x)
+    if (pos[byrank[k]] < 0) atomicMin(out, (int)k);
 }
 
 // one BFS level over unnumbered nodes, order-free (pseudo-peripheral search); warp per node
@@ -205,7 +205,7 @@ __global__ void last_sum_k(const int* __restrict__ off, const int* __restrict__ 
   out[0] = off[k - 1] + cnt[k - 1];
 }
 __global__ void reverse_k(int n, const int* __restrict__ order, int* __restrict__ perm) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = order[n - 1 - i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) perm[i] = order[n - 1 - i];
 }
 __global__ void set_one_k(int* __restrict__ order, int* __restrict__ pos, int at, int v) {
   order[at] = v;
@@ -218,10 +218,10 @@ __global__ void bfs_seed_k(int* __restrict__ front, int* __restrict__ mark, int 
 
 // ---- permutation
 __global__ void iperm_k(int n, const int* __restrict__ perm, int* __restrict__ iperm) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) iperm[perm[i]] = i;
 }
 __global__ void ulen_k(int n, const int* __restrict__ perm, const int* __restrict__ rp, int* __restrict__ len) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     len[i] = rp[perm[i] + 1] - rp[perm[i]];
 }
 __global__ void ufill_k(int n, const int* __restrict__ perm, const int* __restrict__ iperm, const int* __restrict__ rp,
@@ -240,7 +240,7 @@ __global__ void ufill_k(int n, const int* __restrict__ perm, const int* __restri
 template <typename T>
 __global__ void gather_src_k(int nnz, const int* __restrict__ p2, const int* __restrict__ p1,
                              const int* __restrict__ usrc, const T* __restrict__ vals, T* __restrict__ out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += gridDim.x * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (long long)gridDim.x * blockDim.x)
     out[i] = vals[usrc[p1[p2[i]]]];
 }
 

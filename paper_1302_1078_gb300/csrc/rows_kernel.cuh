@@ -94,8 +94,10 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
       return s_val[i];
   };
 
-  for (int c0 = bs; c0 < be; c0 += tile) {
-    const int c1 = min(be, c0 + tile);
+  // passes over the block's nonzeros [bs, be), tile at a time (c0 + tile is never formed past be,
+  // so positions near 2^31 do not overflow)
+  for (int c0 = bs, c1 = 0; c0 < be; c0 = c1) {
+    c1 = be - c0 > tile ? c0 + tile : be;
     const int a0 = c0 & ~3;
     if constexpr (PERM)
       stage_copy<int>(reinterpret_cast<int*>(s_val), a.perm, a0, c1, a.aligned_vals, pol_stream);

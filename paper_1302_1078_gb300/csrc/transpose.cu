@@ -28,17 +28,17 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
 
 __global__ void iota_kernel(int* __restrict__ out, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = i;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) out[i] = i;
 }
 
 // Row of every nonzero: one warp per row writes the row id over its range.
 __global__ void expand_rows_kernel(const int* __restrict__ row_ptr, int m, int* __restrict__ rows) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int i = warp; i < m; i += nwarps) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < m; i += nwarps) {
     const int s = row_ptr[i], e = row_ptr[i + 1];
-    for (int p = s + lane; p < e; p += 32) rows[p] = i;
+    for (int p = s + lane; p < e; p += 32) rows[p] = (int)i;
   }
 }
 
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(const int* __res
 
 // row_ptr of A^T from the sorted column ids: rptrT[j] = first position whose key >= j.
 __global__ void boundaries_kernel(const int* __restrict__ skeys, int nnz, int n, int* __restrict__ rptrT) {
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= nnz; q += gridDim.x * blockDim.x) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q <= nnz; q += (long long)gridDim.x * blockDim.x) {
     const int lo = q == 0 ? 0 : skeys[q - 1] + 1;  // first column starting at q
     const int hi = q == nnz ? n : skeys[q];         // last column starting at q
     for (int j = lo; j <= hi; ++j) rptrT[j] = q;
@@ -124,12 +124,12 @@ __global__ void boundaries_kernel(const int* __restrict__ skeys, int nnz, int n,
 }
 
 __global__ void gather_int_kernel(const int* __restrict__ src, const int* __restrict__ idx, int n, int* __restrict__ out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = src[idx[i]];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) out[i] = src[idx[i]];
 }
 
 template <typename T>
 __global__ void gather_vals_kernel(const T* __restrict__ src, const int* __restrict__ idx, int n, T* __restrict__ out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = src[idx[i]];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) out[i] = src[idx[i]];
 }
 
 static int grid_for(long long work, int threads = 256) {

@@ -78,6 +78,13 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.spmv_bcsr(None, None, None, None) == _capi.GBS_EINVAL
     assert lib.gbs_bcsr_destroy(None) == _capi.GBS_OK
     assert lib.spmv_csr_batched_plan_cfg(None, 1, None, 0, 1, 0, None, None) == _capi.GBS_EINVAL
+    # size limit m + nnz <= 2^31 - 4097: one past it is refused on the host, for every kind of call
+    big = 2**31 - 4096
+    assert lib.spmv_csr(1, 4, big - 1, 16, 16, 16, 0, 16, 16, None) == _capi.GBS_EUNSUPPORTED
+    assert b"2^31 - 4097" in lib.gbs_last_error()
+    assert lib.gbs_plan_create(ctypes.byref(h), 1, 4, big - 1, 16, 16, 0, 1, 0, None) == _capi.GBS_EUNSUPPORTED
+    assert lib.gbs_transpose_plan(ctypes.byref(h), 1, 4, big - 1, 16, 16, None) == _capi.GBS_EUNSUPPORTED
+    assert lib.gbs_ucld(1, 4, big - 1, 16, 16, 8, None, None, None, None) == _capi.GBS_EUNSUPPORTED
 
 
 def test_default_config_host_only(lib):
