@@ -151,6 +151,19 @@ int gbs_default_config(const gbs_stats* stats, int dtype, int k, gbs_config* out
 int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream);
 
 /*
+ * Diagnostic for the failure path of the bounded device waits.  ROWS_TMA's
+ * CTAs wait on mbarriers for their bulk copies; every such wait gives up
+ * after 1 s of GPU global time (or 2^22 polls should the timer not advance),
+ * flags the plan's status word (gbs_plan_status then returns GBS_ETIMEOUT)
+ * and returns, so the context stays usable.  This call runs one such wait on
+ * a barrier that nothing completes (a 16-byte copy is announced and never
+ * issued), bounded by limit_ns (1 .. 2e9), on `stream`, and synchronises it.
+ * Returns GBS_ETIMEOUT when the wait gave up, which is the expected result;
+ * GBS_EINVAL for a limit out of range.  The paper has no counterpart.
+ */
+int gbs_wait_probe(long long limit_ns, void* stream);
+
+/*
  * Diagnostic: useful cacheline density (UCLD, Sec. 4.1, the figure that ties
  * the gain of vectorised SpMV to it).  x is cut into aligned lines of
  * `line_elems` elements (line j = x[j*line_elems .. (j+1)*line_elems - 1]); a

@@ -61,6 +61,7 @@ class gbs_stats(ctypes.Structure):
 SIGNATURES = {
     "gbs_version": (I32, []),
     "gbs_fp64_probe": (I32, [P, I32, I32, I32, P]),
+    "gbs_wait_probe": (I32, [I64, P]),
     "gbs_status_string": (ctypes.c_char_p, [I32]),
     "gbs_last_error": (ctypes.c_char_p, []),
     "gbs_validate_csr": (I32, [I32, I32, I32, P, P, P]),

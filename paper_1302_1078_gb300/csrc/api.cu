@@ -322,6 +322,22 @@ int compute_stats(int m, int n, int nnz, const int* rp, gbs_stats* out, cudaStre
   return GBS_OK;
 }
 
+// A wait that runs out on purpose, for testing the timeout path: one CTA arms an mbarrier for a
+// 16-byte copy that is never issued and waits on it (bounded by limit_ns); status[0] = 1 when
+// the wait gave up, 0 if it completed.
+__global__ void wait_probe_kernel(int* __restrict__ status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (threadIdx.x == 0) status[0] = ok ? 0 : 1;
+}
+
 __global__ void block_max_nnz_kernel(const int* __restrict__ rp, int m, int rpc, int* __restrict__ out) {
   const int nb = (m + rpc - 1) / rpc;
   int mx = 0;
@@ -425,6 +441,26 @@ cudaError_t launch_merge_partition(const CsrView& A, long long items_per_cta, co
 extern "C" {
 
 int gbs_version(void) { return 100; }
+
+int gbs_wait_probe(long long limit_ns, void* stream) {
+  if (limit_ns < 1 || limit_ns > 2000000000LL) return fail(GBS_EINVAL, "limit_ns must be in [1, 2e9]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (wait probe)");
+  e = cudaMemsetAsync(d, 0xff, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(d, (unsigned long long)limit_ns);
+    e = cudaGetLastError();
+  }
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  if (h == 1) return fail(GBS_ETIMEOUT, "wait probe: the bounded wait gave up (expected)");
+  return h == 0 ? GBS_OK : fail(GBS_ECUDA, "wait probe: no status written");
+}
 
 int gbs_fp64_probe(double* out, int blocks, int threads, int iters, void* stream) {
   if (!out || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || iters < 1)

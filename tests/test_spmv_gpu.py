@@ -235,6 +235,31 @@ def test_zero_rows_and_zero_columns(gbs):
     assert torch.equal(y, torch.zeros(5, dtype=torch.float64, device="cuda"))
 
 
+
+def test_bounded_wait_times_out_and_context_stays_usable(gbs):
+    """A device wait that nothing completes gives up at its limit and reports GBS_ETIMEOUT; the
+    next products on the same context are still right (no fault, no hang)."""
+    import time
+
+    from paper_1302_1078_gb300 import _capi
+
+    stream = torch.cuda.current_stream().cuda_stream
+    assert gbs.lib().gbs_wait_probe(0, stream) == _capi.GBS_EINVAL
+    t0 = time.perf_counter()
+    assert gbs.lib().gbs_wait_probe(20_000_000, stream) == _capi.GBS_ETIMEOUT  # 20 ms
+    dt = time.perf_counter() - t0
+    assert 0.019 <= dt < 5.0, dt
+    A = matrix("stencil3d_21")
+    rp, ci, v = dev_csr(A)
+    x = synth.uniform(A.n, seed=5)
+    y_ref, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, 1, config=dict(variant=_capi.VARIANT_ROWS_TMA, lanes=4, threads=128))
+    y = plan.spmv(v, torch.from_numpy(x).cuda())
+    assert_close(y, y_ref, r, torch.float64, "after the timed-out wait")
+    st = ctypes.c_int(-1)
+    gbs.lib().gbs_plan_status(plan._h, ctypes.byref(st), stream)
+    assert st.value == 0
+
 # ------------------------------------------------ full-size configurations
 
 FULL = {
