@@ -71,6 +71,26 @@ def _check_index(row_ptr: torch.Tensor, col_idx: torch.Tensor):
         raise ValueError("row_ptr and col_idx must be contiguous 1-D tensors")
 
 
+def _check_vals(vals: torch.Tensor, nnz: int):
+    """The kernels read vals as nnz contiguous entries."""
+    if vals.dim() != 1 or vals.numel() != nnz or not vals.is_contiguous():
+        raise ValueError(f"vals must be a contiguous 1-D tensor of nnz = {nnz} entries")
+
+
+def _check_vector(t: torch.Tensor, size: int, dtype, what: str, exact: bool):
+    if t.dtype != dtype or t.dim() != 1 or not t.is_contiguous() or (t.numel() != size if exact else t.numel() < size):
+        need = f"{size}" if exact else f"at least {size}"
+        raise ValueError(f"{what} must be a contiguous 1-D {dtype} tensor of {need} entries")
+
+
+def _check_block(t: torch.Tensor, rows: int, k: int, dtype, what: str, exact: bool):
+    """A row-major rows x k block; its row stride may exceed k."""
+    if (t.dtype != dtype or t.dim() != 2 or t.shape[1] != k or t.stride(1) != 1 or
+            (t.shape[0] != rows if exact else t.shape[0] < rows)):
+        need = f"{rows}" if exact else f"at least {rows}"
+        raise ValueError(f"{what} must be a row-major 2-D {dtype} tensor of {need} rows and {k} columns")
+
+
 def _config(cfg) -> gbs_config | None:
     if cfg is None:
         return None
@@ -85,12 +105,12 @@ def _config(cfg) -> gbs_config | None:
 def spmv_csr(row_ptr, col_idx, vals, x, y=None, *, n: int | None = None, config=None, stream=None):
     """y <- A x for the CSR matrix (row_ptr, col_idx, vals).  Returns y."""
     _check_index(row_ptr, col_idx)
+    _check_vals(vals, col_idx.numel())
+    n = x.numel() if n is None else n
+    _check_vector(x, n, vals.dtype, "x", exact=False)
     dev = _need_cuda(row_ptr, col_idx, vals, x, y)
     dt = _dtype_code(vals)
-    if x.dtype != vals.dtype or x.dim() != 1 or not x.is_contiguous():
-        raise ValueError("x must be a contiguous 1-D tensor of the values' dtype")
     m = row_ptr.numel() - 1
-    n = x.numel() if n is None else n
     if y is None:
         y = torch.empty(m, dtype=vals.dtype, device=dev)
     elif y.dtype != vals.dtype or y.numel() != m or not y.is_contiguous():
@@ -110,6 +130,7 @@ def spmv_csr(row_ptr, col_idx, vals, x, y=None, *, n: int | None = None, config=
 def spmm_csr(row_ptr, col_idx, vals, X, Y=None, *, config=None, stream=None):
     """Y <- A X with X an n x k row-major tensor (a row stride >= k is allowed).  Returns Y."""
     _check_index(row_ptr, col_idx)
+    _check_vals(vals, col_idx.numel())
     dev = _need_cuda(row_ptr, col_idx, vals, X, Y)
     dt = _dtype_code(vals)
     if X.dtype != vals.dtype or X.dim() != 2 or X.stride(1) != 1:
@@ -314,16 +335,22 @@ class Plan:
             y = torch.empty(self.m, dtype=self.dtype, device=self.device)
         if vals.dtype != self.dtype or x.dtype != self.dtype or y.dtype != self.dtype:
             raise TypeError("dtype differs from the plan's")
+        _check_vals(vals, self.nnz)
+        _check_vector(x, self.n, self.dtype, "x", exact=False)
+        _check_vector(y, self.m, self.dtype, "y", exact=True)
         _capi.check(lib().spmv_csr_plan(self._h, _ptr(vals), _ptr(x), _ptr(y), _stream(self.device, stream)),
                     "spmv_csr_plan")
         return y
 
     def spmm(self, vals, X, Y=None, stream=None):
         _need_cuda(vals, X, Y)
-        if X.dim() != 2 or X.shape[1] != self.k or X.stride(1) != 1:
-            raise ValueError("X must be n x k row major")
+        if vals.dtype != self.dtype:
+            raise TypeError("dtype differs from the plan's")
+        _check_vals(vals, self.nnz)
+        _check_block(X, self.n, self.k, self.dtype, "X", exact=False)
         if Y is None:
             Y = torch.empty((self.m, self.k), dtype=self.dtype, device=self.device)
+        _check_block(Y, self.m, self.k, self.dtype, "Y", exact=True)
         _capi.check(lib().spmm_csr_plan(self._h, _ptr(vals), _ptr(X), max(X.stride(0), self.k), _ptr(Y),
                                         max(Y.stride(0), self.k), _stream(self.device, stream)), "spmm_csr_plan")
         return Y
@@ -386,6 +413,10 @@ class TransposePlan:
         """(dX, dvals) of Y = A X for upstream dY; X and dY are 1-D (SpMV) or 2-D row major."""
         _need_cuda(vals, X, dY)
         dt = _dtype_code(vals)
+        _check_vals(vals, self.nnz)
+        if X.dim() != dY.dim() or X.dim() not in (1, 2) or X.shape[0] != self.n or dY.shape[0] != self.m or \
+                (X.dim() == 2 and X.shape[1] != dY.shape[1]):
+            raise ValueError(f"X must be n = {self.n} by k and dY m = {self.m} by k (both 1-D for k = 1)")
         vec = X.dim() == 1
         k = 1 if vec else X.shape[1]
         if X.dtype != vals.dtype or dY.dtype != vals.dtype:

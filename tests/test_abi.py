@@ -97,3 +97,28 @@ def test_default_config_host_only(lib):
     st2 = _capi.gbs_stats(m=1000, n=1000, nnz=16000, max_row=5000, empty_rows=300, mean_row=16.0, cv_row=8.0)
     assert lib.gbs_default_config(ctypes.byref(st2), 0, 1, ctypes.byref(c)) == 0
     assert c.variant == _capi.VARIANT_MERGE
+
+
+def test_binding_checks_operands_before_any_call():
+    """The Python binding refuses operands the kernels would read out of bounds, before it
+    touches the library or a device (so this runs on the CPU)."""
+    import torch
+
+    import paper_1302_1078_gb300 as gbs
+
+    rp = torch.tensor([0, 2, 3], dtype=torch.int32)
+    ci = torch.tensor([0, 1, 1], dtype=torch.int32)
+    x = torch.zeros(2, dtype=torch.float64)
+    with pytest.raises(ValueError, match="vals"):
+        gbs.spmv_csr(rp, ci, torch.zeros(2, dtype=torch.float64), x)  # nnz = 3
+    with pytest.raises(ValueError, match="vals"):
+        gbs.spmv_csr(rp, ci, torch.zeros(6, dtype=torch.float64)[::2], x)  # not contiguous
+    with pytest.raises(ValueError, match="x must"):
+        gbs.spmv_csr(rp, ci, torch.zeros(3, dtype=torch.float64), x, n=4)  # x shorter than n
+    with pytest.raises(ValueError, match="x must"):
+        gbs.spmv_csr(rp, ci, torch.zeros(3, dtype=torch.float64), x.float())  # dtype
+    with pytest.raises(ValueError, match="vals"):
+        gbs.spmm_csr(rp, ci, torch.zeros(4, dtype=torch.float64), torch.zeros(2, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA"):  # well-formed host tensors: refused as not on a GPU
+        gbs.spmv_csr(rp, ci, torch.zeros(3, dtype=torch.float64), x)
+
