@@ -17,8 +17,9 @@
 // last <= 3 nonzeros of the arrays, which cannot be rounded up without
 // reading past the end, are loaded with plain loads.
 //
-// Every wait is bounded: on timeout the kernel sets the device error flag,
-// waits (again bounded) for the copies it issued, and returns.
+// Every wait is bounded (1 s of GPU global time, with a poll count as a backstop): on timeout
+// the kernel sets the device error flag, waits (again bounded) for the copies it issued, and
+// returns.
 //
 // EMUL (FP64 only): in every unrolled group of 4 nonzeros, the first EMUL
 // products run on the FP32 pipe (df64.cuh) and the rest on the FP64 pipe.
