@@ -260,6 +260,29 @@ def test_bounded_wait_times_out_and_context_stays_usable(gbs):
     gbs.lib().gbs_plan_status(plan._h, ctypes.byref(st), stream)
     assert st.value == 0
 
+
+def test_checked_mode_refuses_a_bad_structure_before_the_product(gbs, monkeypatch):
+    """GBSPMV_CHECKED=1 validates the CSR structure before every product and returns GBS_EINDEX
+    without launching it; a plan built with check=True refuses the structure at creation."""
+    from paper_1302_1078_gb300 import _capi
+
+    A = matrix("random_rect")
+    rp, ci, v = dev_csr(A)
+    bad = ci.clone()
+    bad[3] = A.n  # one column id out of range
+    # x padded past n, so that even an unchecked product would read inside the allocation
+    x = torch.zeros(A.n + 64, dtype=torch.float64, device="cuda")
+    monkeypatch.setenv("GBSPMV_CHECKED", "1")
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.spmv_csr(rp, bad, v, x, n=A.n)
+    assert e.value.status == _capi.GBS_EINDEX
+    y = gbs.spmv_csr(rp, ci, v, x, n=A.n)  # a valid structure passes in checked mode
+    assert torch.equal(y, torch.zeros(A.m, dtype=torch.float64, device="cuda"))
+    monkeypatch.delenv("GBSPMV_CHECKED")
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.Plan(rp, bad, A.n, torch.float64, 1, check=True)
+    assert e.value.status == _capi.GBS_EINDEX
+
 # ------------------------------------------------ full-size configurations
 
 FULL = {
