@@ -246,7 +246,12 @@ int gbs_bcsr_destroy(gbs_bcsr* plan);
  * y has m entries.  The variant is chosen without looking at row_ptr
  * (merge-path, which balances any row-length distribution); its scratch
  * (one carry per CTA) comes from the stream-ordered allocator of the
- * current device (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * current device (cudaMallocAsync / cudaFreeAsync on `stream`).  This
+ * one-shot call never reads the row-length statistics, because reading them
+ * back would synchronise `stream` on every call.  A plan (gbs_plan_create)
+ * is the path that picks the kernel and the lanes per row from the row
+ * lengths, once: row-wise with lanes from the mean row length for regular
+ * matrices, merge-path for skewed ones, or the autotuner's choice.
  * m, n >= 0, nnz >= 0; nnz == 0 or m == 0 writes zeros / nothing.
  */
 int spmv_csr(int m, int n, int nnz, const int* row_ptr, const int* col_idx, const void* vals,
@@ -275,7 +280,11 @@ int spmv_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, 
  *
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it: make that first call before any
- * stream capture.  Every call shares the one array, whose contents persist
+ * stream capture.  The cached address belongs to the device's current
+ * context: after cudaDeviceReset (or any teardown of the primary context)
+ * the module may be loaded at another address, so do not call this entry
+ * point again in that process.  Misaligned arrays return GBS_EALIGN, as in
+ * spmv_csr, before anything is launched.  Every call shares the one array, whose contents persist
  * from the previous call; each call writes every scratch element before
  * reading it, so nothing needs clearing.  Calls that overlap on the GPU (on
  * different streams, or from different threads without ordering) race on

@@ -86,6 +86,15 @@ extern "C" int spmv_csr_noalloc(int m, int n, int nnz, const int* row_ptr, const
     set_last_error("spmv_csr_noalloc: NULL pointer");
     return GBS_EINVAL;
   }
+  // the same alignment rule as spmv_csr: every array aligned to its element size, refused on
+  // the host so that a misaligned pointer never reaches a kernel
+  const uintptr_t es = dtype == GBS_F64 ? sizeof(double) : sizeof(float);
+  if ((reinterpret_cast<uintptr_t>(vals) % es) || (reinterpret_cast<uintptr_t>(x) % es) ||
+      (reinterpret_cast<uintptr_t>(y) % es) || (reinterpret_cast<uintptr_t>(col_idx) % 4) ||
+      (reinterpret_cast<uintptr_t>(row_ptr) % 4)) {
+    set_last_error("spmv_csr_noalloc: arrays must be aligned to their element size");
+    return GBS_EALIGN;
+  }
   const long long total = (long long)m + nnz;
   const long long ipc = (long long)kNoAllocThreads * kNoAllocItems;
   const long long ctas = std::max<long long>(1, (total + ipc - 1) / ipc);

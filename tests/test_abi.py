@@ -87,6 +87,26 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gbs_ucld(1, 4, big - 1, 16, 16, 8, None, None, None, None) == _capi.GBS_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("entry", ["spmv_csr", "spmv_csr_noalloc"])
+def test_misaligned_pointers_are_refused_on_the_host(lib, entry):
+    """A pointer off its element size is refused with GBS_EALIGN before any CUDA call (the
+    pointers are never dereferenced, so no GPU is needed): vals, x, y at an odd byte offset
+    for FP64 and FP32, and row_ptr / col_idx off 4 bytes."""
+    from paper_1302_1078_gb300 import _capi
+
+    f = getattr(lib, entry)
+    ok = 4096
+    for dt in (_capi.GBS_F64, _capi.GBS_F32):
+        for bad in range(5):
+            args = [ok, ok, ok, ok, ok]  # row_ptr, col_idx, vals, x, y
+            args[bad] = ok + 2
+            rp, ci, v, x, y = args
+            assert f(8, 8, 16, rp, ci, v, dt, x, y, None) == _capi.GBS_EALIGN, (dt, bad)
+            assert b"aligned" in lib.gbs_last_error()
+    # FP64 arrays 4 bytes off: aligned for FP32 but not for FP64
+    assert f(8, 8, 16, ok, ok, ok + 4, _capi.GBS_F64, ok, ok, None) == _capi.GBS_EALIGN
+
+
 def test_default_config_host_only(lib):
     from paper_1302_1078_gb300 import _capi
 

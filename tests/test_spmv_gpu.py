@@ -200,6 +200,33 @@ def test_plans_and_tuner(gbs, k):
                 assert_close(plan.spmm(v, torch.from_numpy(X).cuda()), Y_ref, R, torch.float64, f"{name} {cfg}")
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_untuned_plan_picks_the_kernel_from_row_lengths(gbs, dtype):
+    """A plan without tuning chooses its kernel from the row-length statistics: row-wise with
+    lanes from the mean row length for the stencil and banded matrices, merge-path for the
+    power-law R-MAT.  The one-shot spmv_csr (no statistics, no synchronisation) is merge-path
+    everywhere; both agree with the oracle."""
+    from paper_1302_1078_gb300 import _capi
+
+    want = {"stencil3d_21": {_capi.VARIANT_ROWS}, "banded_30k": {_capi.VARIANT_ROWS},
+            "rmat_14": {_capi.VARIANT_MERGE, _capi.VARIANT_MERGE_DIRECT}}
+    for name, variants in want.items():
+        A = matrix(name)
+        rp, ci, v = dev_csr(A, dtype)
+        x = synth.uniform(A.n, seed=12)
+        y_ref, r = spmv_ref(A, x, dtype)
+        xd = torch.from_numpy(x.astype(NP[dtype])).cuda()
+        plan = gbs.Plan(rp, ci, A.n, dtype, 1)
+        cfg = plan.config
+        assert cfg["variant"] in variants, (name, cfg)
+        mean = A.nnz / A.m
+        if cfg["variant"] == _capi.VARIANT_ROWS:
+            per = 64 if dtype == torch.float64 else 16
+            assert cfg["lanes"] == 1 or mean > per * (cfg["lanes"] // 2), (name, cfg)
+        assert_close(plan.spmv(v, xd), y_ref, r, dtype, f"untuned plan {name} {cfg}")
+        assert_close(gbs.spmv_csr(rp, ci, v, xd), y_ref, r, dtype, f"one-shot {name}")
+
+
 def test_stats_and_validation(gbs):
     from paper_1302_1078_gb300 import _capi
 

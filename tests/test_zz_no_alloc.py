@@ -1,10 +1,18 @@
 """spmv_csr_noalloc: the SpMV entry point for callers that must not allocate device memory
 (for example a host application that owns every device allocation, or a latency-critical
 loop where an allocation could block or fail).  Its scratch is a static array inside the
-library.  The test calls it through the C ABI and compares it with spmv_csr on two calls in
-a row (different matrices, so the second call runs over the first call's leftover scratch),
-within the parity bound the other tests use.  It needs nothing from the other test files,
-so it passes alone in a fresh process as well as after them."""
+library.
+
+The test calls it through the C ABI on two calls in a row (different matrices, so the
+second call runs over the first call's leftover scratch) and checks each result
+  * against the CPU oracle's y, within the parity bound the other tests use;
+  * bit for bit against spmv_csr, which runs the same merge-path configuration (256
+    threads, 15 items per thread, the same partition and carry fix-up) with scratch from
+    the stream-ordered allocator; a stale carry left in the shared array would show here;
+and checks that the two calls allocated nothing: the high-water mark of the device's
+default memory pool (where spmv_csr's scratch comes from) does not move, and neither does
+the device's free memory.  It needs nothing from the other test files, so it passes alone
+in a fresh process as well as after them."""
 import ctypes
 
 import numpy as np
@@ -18,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
 NP = {torch.float64: np.float64, torch.float32: np.float32}
+POOL_USED_HIGH = 8  # cudaMemPoolAttrUsedMemHigh
 
 
 def _noalloc(lib, A, v, x, y, dtype):
@@ -31,27 +40,86 @@ def _dev(M: synth.CSR):
     return dict(m=M.m, n=M.n, nnz=M.nnz, rp=torch.from_numpy(M.row_ptr).cuda(), ci=torch.from_numpy(M.col_idx).cuda())
 
 
+def _cudart():
+    """The CUDA runtime, loaded on its own, for the memory-pool counters (None if absent)."""
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+        except OSError:
+            continue
+        rt.cudaDeviceGetDefaultMemPool.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+        rt.cudaMemPoolGetAttribute.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        rt.cudaMemPoolSetAttribute.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        return rt
+    return None
+
+
+class _PoolHigh:
+    """High-water mark of bytes in use from the current device's default memory pool."""
+
+    def __init__(self, rt):
+        self.rt = rt
+        self.pool = ctypes.c_void_p()
+        assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(self.pool), torch.cuda.current_device()) == 0
+
+    def reset(self):
+        zero = ctypes.c_uint64(0)  # resets the mark to the bytes in use now
+        assert self.rt.cudaMemPoolSetAttribute(self.pool, POOL_USED_HIGH, ctypes.byref(zero)) == 0
+
+    def value(self) -> int:
+        v = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, POOL_USED_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
-def test_noalloc_matches_spmv_csr_on_two_calls(dtype):
+def test_noalloc_matches_oracle_and_spmv_csr_on_two_calls(dtype):
     import paper_1302_1078_gb300 as gbs
 
     lib = gbs.lib()
     # the larger matrix first, then a smaller one: the second call reuses scratch the first left behind
     mats = [synth.rmat(15, ef=16, seed=7), synth.banded(20011, hbw=500, per_row=21, seed=8)]
+    cases = []
     for i, M in enumerate(mats):
         A = _dev(M)
-        v = torch.from_numpy(M.vals.astype(NP[dtype])).cuda()
+        vh = M.vals.astype(NP[dtype])
         xh = synth.uniform(M.n, seed=9, stream=i).astype(NP[dtype])
-        x = torch.from_numpy(xh).cuda()
+        v, x = torch.from_numpy(vh).cuda(), torch.from_numpy(xh).cuda()
+        # spmv_csr's result first (it allocates its scratch from the pool), outside the window below
+        y_ref = gbs.spmv_csr(A["rp"], A["ci"], v, x)
         y = torch.full((M.m,), float("nan"), dtype=dtype, device="cuda")
+        cases.append((M, A, vh, xh, v, x, y, y_ref))
+    # the first call on a device looks up the static array's address, which loads the module that
+    # holds it: made here, before the measured window, as the header asks of a first call
+    M0 = synth.stencil2d(8)
+    A0 = _dev(M0)
+    v0 = torch.from_numpy(M0.vals.astype(NP[dtype])).cuda()
+    x0 = torch.ones(M0.n, dtype=dtype, device="cuda")
+    y0 = torch.empty(M0.m, dtype=dtype, device="cuda")
+    assert _noalloc(lib, A0, v0, x0, y0, dtype) == 0, lib.gbs_last_error()
+    torch.cuda.synchronize()
+
+    rt = _cudart()
+    pool = _PoolHigh(rt) if rt is not None else None
+    if pool is not None:
+        pool.reset()
+        high0 = pool.value()
+    free0 = torch.cuda.mem_get_info()[0]
+    for i, (M, A, vh, xh, v, x, y, y_ref) in enumerate(cases):
         rc = _noalloc(lib, A, v, x, y, dtype)
         assert rc == 0, lib.gbs_last_error()
-        y_ref = gbs.spmv_csr(A["rp"], A["ci"], v, x)
-        torch.cuda.synchronize()
-        _, r = oracle.spmv(M.m, M.row_ptr, M.col_idx, M.vals.astype(NP[dtype]), xh)
-        got, ref = y.double().cpu().numpy(), y_ref.double().cpu().numpy()
-        assert np.all(np.abs(got - ref) <= TOL[dtype] * r), f"call {i}: differs from spmv_csr"
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    if pool is not None:
+        assert pool.value() == high0, "the no-allocation entry point drew memory from the default pool"
+    assert free1 >= free0, "device memory in use grew across the two calls"
+
+    for i, (M, A, vh, xh, v, x, y, y_ref) in enumerate(cases):
+        y_orc, r = oracle.spmv(M.m, M.row_ptr, M.col_idx, vh, xh)
+        got = y.double().cpu().numpy()
+        assert np.all(np.abs(got - y_orc) <= TOL[dtype] * r), f"call {i}: outside the bound of the oracle"
         assert np.all(got[r == 0] == 0.0)
+        assert torch.equal(y, y_ref), f"call {i}: not bitwise equal to spmv_csr's merge-path result"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -59,7 +127,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
 
     lib = gbs.lib()
     # m + nnz = 1.2e9 needs more scratch than the static array holds: rejected before any launch,
-    # so the (never dereferenced) pointers may be anything non-NULL
+    # so the (never dereferenced) pointers may be anything non-NULL and aligned
     rc = lib.spmv_csr_noalloc(600_000_000, 600_000_000, 600_000_000, 16, 16, 16, 0, 16, 16, None)
     assert rc == -8  # GBS_EUNSUPPORTED
     assert b"static scratch" in lib.gbs_last_error()
