@@ -27,6 +27,10 @@ Parity status of each entry point (the pins are in ``tests/test_oracle.py``):
   closed-form block counts (identity, dense, block-diagonal) and the fill of a dense block.
 * ``ucld``: pinned by the paper's worked example (Sec. 4.1, row 0 19 20 -> 3/16),
   its two extremes (1/line and 1) and brute force on tiny matrices.
+* ``degree_relabel``: pinned by closed forms (full lower and upper triangles give the
+  identity and the reversal, a permutation matrix ties everywhere and gives the
+  identity), numpy's lexsort on random matrices with repeated entries, and the
+  invariant that the relabelled product equals the original one bitwise.
 """
 from __future__ import annotations
 
@@ -80,6 +84,8 @@ def _load():
             lib.orc_bcsr.argtypes = [i32, i32, P, P, P, i32, i32, P, P, P]
             lib.orc_bcsr.restype = ll
             lib.orc_bcsr_spmv.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P]
+            lib.orc_degree_relabel.argtypes = [i32, i32, P, P]
+            lib.orc_degree_relabel.restype = i32
             lib.orc_max_threads.restype = i32
             _lib = lib
     return _lib
@@ -246,3 +252,17 @@ def bcsr_spmv(m, n, a, b, bptr, bcol, bval, x):
     y, r = np.empty(int(m)), np.empty(int(m))
     lib.orc_bcsr_spmv(int(m), int(n), int(a), int(b), _p(bptr), _p(bcol), _p(bval), _p(x), _p(y), _p(r))
     return y, r
+
+
+def degree_relabel(n, col_idx):
+    """newid[j] = rank of column j when the columns are ordered by stored entries, most first,
+    ties by ascending column id (the relabelling of oracle.c's orc_degree_relabel)."""
+    lib = _load()
+    ci = _c(col_idx, np.int32)
+    newid = np.empty(max(int(n), 0), np.int32)
+    rc = lib.orc_degree_relabel(int(n), int(ci.size), _p(ci), _p(newid))
+    if rc == -1:
+        raise ValueError("column index out of range")
+    if rc != 0:
+        raise MemoryError("orc_degree_relabel")
+    return newid

@@ -533,6 +533,46 @@ int orc_permute(int n, const int* rptrs, const int* cids, const double* val, con
   return 0;
 }
 
+/* ------------------------------------------------- degree relabelling */
+
+/*
+ * Column relabelling by in-degree, hottest column first.  Sec. 4.1 and
+ * Sec. 4.3 tie SpMV speed to how well the x accesses reuse cache lines, and
+ * Sec. 4.4 reorders the matrix to improve that reuse; this is the column-only
+ * reordering whose target is the reuse of the most frequently gathered x
+ * entries (it leaves the rows, and so y, in place):
+ *   deg[j]   = number of stored entries in column j;
+ *   the columns are ranked by deg descending, ties by ascending column id;
+ *   newid[j] = the rank of column j, 0 for the hottest.
+ * The relabelled matrix keeps every row's entries in storage order with
+ * cids'[p] = newid[cids[p]], and x'[newid[j]] = x[j], so that A' x' = A x
+ * term by term.  Returns 0, -1 if a column id is outside [0, n), or -2 if a
+ * scratch allocation fails.
+ */
+static const int* g_rl_deg; /* comparison context for qsort */
+static int cmp_hot_first(const void* a, const void* b) {
+  const int ja = *(const int*)a, jb = *(const int*)b;
+  if (g_rl_deg[ja] != g_rl_deg[jb]) return g_rl_deg[ja] > g_rl_deg[jb] ? -1 : 1; /* more entries first */
+  return (ja > jb) - (ja < jb);                                                   /* then by column id */
+}
+
+int orc_degree_relabel(int n, int nnz, const int* cids, int* newid) {
+  int* deg = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
+  int* order = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!deg || !order) { free(deg); free(order); return -2; }
+  for (int p = 0; p < nnz; ++p) {
+    if (cids[p] < 0 || cids[p] >= n) { free(deg); free(order); return -1; }
+    deg[cids[p]] += 1;
+  }
+  for (int j = 0; j < n; ++j) order[j] = j;
+  g_rl_deg = deg;
+  qsort(order, (size_t)n, sizeof(int), cmp_hot_first);
+  for (int q = 0; q < n; ++q) newid[order[q]] = q;
+  free(deg);
+  free(order);
+  return 0;
+}
+
 /* ----------------------------------------------------------------- BCSR */
 
 /*

@@ -665,6 +665,119 @@ def test_rcm_planted_mistakes_are_caught(tmp_path, monkeypatch, name, old, new):
     assert caught >= 1, f"no pin caught the planted mistake: {name}"
 
 
+# ------------------------------------------------------- degree relabelling
+
+def _lower_full(n):
+    rp = np.concatenate([[0], np.cumsum(np.arange(1, n + 1))]).astype(np.int32)
+    ci = np.concatenate([np.arange(i + 1) for i in range(n)]).astype(np.int32)
+    return rp, ci
+
+
+def check_relabel_closed_forms(relabel):
+    n = 9
+    # full lower triangle: column j holds n - j entries, so the order is the identity
+    _, ci = _lower_full(n)
+    assert np.array_equal(relabel(n, ci), np.arange(n))
+    # full upper triangle: column j holds j + 1 entries, so the hottest is the last column
+    ci_up = np.concatenate([np.arange(i, n) for i in range(n)]).astype(np.int32)
+    assert np.array_equal(relabel(n, ci_up), np.arange(n)[::-1])
+    # a permutation matrix: every column once, all ties, so ties by column id give the identity
+    perm = np.random.default_rng(3).permutation(n).astype(np.int32)
+    assert np.array_equal(relabel(n, perm), np.arange(n))
+    # a rectangular matrix with one hub column (5), two columns of two entries (1, 7) and empty
+    # columns: 5 first, then 1 and 7 by id, then the once-used 2, then the empty 0, 3, 4, 6, 8, 9
+    ci = np.array([5, 1, 5, 7, 5, 2, 1, 5, 7], np.int32)
+    want = np.empty(10, np.int32)
+    want[[5, 1, 7, 2, 0, 3, 4, 6, 8, 9]] = np.arange(10)
+    assert np.array_equal(relabel(10, ci), want)
+    # no entries at all: every column ties, identity
+    assert np.array_equal(relabel(4, np.zeros(0, np.int32)), np.arange(4))
+
+
+def check_relabel_brute_force(relabel):
+    for trial in range(6):
+        A = synth.random_csr(40 + trial, 57, 0.1, 600 + trial, sorted_cols=bool(trial % 2), duplicates=True)
+        deg = np.bincount(A.col_idx, minlength=A.n)
+        order = np.lexsort((np.arange(A.n), -deg))  # degree descending, then column id
+        want = np.empty(A.n, np.int64)
+        want[order] = np.arange(A.n)
+        got = relabel(A.n, A.col_idx)
+        assert np.array_equal(got, want), trial
+        assert np.array_equal(np.sort(got), np.arange(A.n))
+
+
+def check_relabel_product_unchanged(relabel):
+    """A' x' = A x bitwise: each row keeps its terms in storage order, with the same values."""
+    for A in (synth.rmat(9, ef=8, seed=610), synth.random_csr(70, 90, 0.07, 611, duplicates=True, empty_rows=0.2)):
+        x = synth.uniform(A.n, seed=612)
+        newid = relabel(A.n, A.col_idx)
+        xp = np.empty_like(x)
+        xp[newid] = x
+        y, r = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals, x)
+        y2, r2 = oracle.spmv(A.m, A.row_ptr, newid[A.col_idx], A.vals, xp)
+        assert np.array_equal(y, y2) and np.array_equal(r, r2)
+
+
+def test_relabel_closed_forms():
+    check_relabel_closed_forms(oracle.degree_relabel)
+
+
+def test_relabel_brute_force():
+    check_relabel_brute_force(oracle.degree_relabel)
+
+
+def test_relabel_product_unchanged():
+    check_relabel_product_unchanged(oracle.degree_relabel)
+
+
+def test_relabel_power_law_puts_the_hub_columns_first():
+    """On R-MAT (a, b, c, d = 0.57, 0.19, 0.19, 0.05) column 0 is the most likely at every level, so
+    it is the hottest; the top 1 % of the relabelled columns hold far more than 1 % of the entries."""
+    A = synth.rmat(14, ef=16, seed=613)
+    newid = oracle.degree_relabel(A.n, A.col_idx)
+    assert newid[0] == 0
+    deg = np.bincount(newid[A.col_idx], minlength=A.n)
+    assert np.all(np.diff(deg) <= 0)
+    assert deg[: A.n // 100].sum() > 0.1 * A.nnz
+
+
+RELABEL_MUTATIONS = [
+    ("coldest first", "return g_rl_deg[ja] > g_rl_deg[jb] ? -1 : 1;", "return g_rl_deg[ja] < g_rl_deg[jb] ? -1 : 1;"),
+    ("ties by descending id", "return (ja > jb) - (ja < jb);                                                   /* then",
+     "return (jb > ja) - (jb < ja);                                                   /* then"),
+    ("order not inverted", "for (int q = 0; q < n; ++q) newid[order[q]] = q;",
+     "for (int q = 0; q < n; ++q) newid[q] = order[q];"),
+    ("repeats counted once", "deg[cids[p]] += 1;", "deg[cids[p]] = 1;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", RELABEL_MUTATIONS, ids=[m[0] for m in RELABEL_MUTATIONS])
+def test_relabel_planted_mistakes_are_caught(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert old in src
+    c = tmp_path / "mut.c"
+    c.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(c), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.orc_degree_relabel.argtypes = [i32, i32, P, P]
+
+    def mutant(n, ci):
+        ci = np.ascontiguousarray(ci, np.int32)
+        newid = np.empty(n, np.int32)
+        lib.orc_degree_relabel(int(n), int(ci.size), ci.ctypes.data if ci.size else 0, newid.ctypes.data)
+        return newid
+
+    caught = 0
+    for check in (check_relabel_closed_forms, check_relabel_brute_force):
+        try:
+            check(mutant)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, f"no pin caught the planted mistake: {name}"
+
+
 # ----------------------------------------------------------------- BCSR
 
 def _bcsr_dense(m, n, a, b, bptr, bcol, bval):
