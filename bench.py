@@ -15,8 +15,14 @@ Reported (one JSON line on rank 0): GFLOP/s = 2 * nnz * k / t over all
 ranks, the per-launch roofline of the dominant kernel against the measured
 HBM copy bandwidth (compulsory bytes, Sec. 4.2: 12 nnz + 4 (m+1) + 8 n k +
 8 m k) and against the FP64 FMA rate measured live (GB300's second roof),
-an end-to-end figure through the public API with host buffers, the CPU
-oracle timed on the host cores, and the SM clocks sampled during timing.
+an end-to-end figure through the public API with host buffers (with the
+host-to-device copy rate measured alone), the CPU oracle timed on the host
+cores, and the SM clocks sampled during timing.  The same line carries the
+rest of the metric, each part timed with its own CUDA events after an L2
+flush: "spmm" (Sec. 5: k = 4, 8, 16 on the sweep's matrices), "batched" (512
+uneven matrices, k = 8, one graph-replayed persistent launch against the
+per-matrix launch loops: batched_vs_looped) and "autograd" (R-MAT scale 20:
+forward, backward, bwd_over_fwd).  --sweep-only skips those three.
 
 --gpus N > 1 runs under torchrun: every rank multiplies its own independent
 matrices (weak scaling, no collective on the data path; one all-reduce of
@@ -121,6 +127,16 @@ def compulsory_bytes(m, n, nnz, k, es=8):
     return (es + 4) * nnz + 4 * (m + 1) + es * n * k + es * m * k
 
 
+def measured_hbm_peak():
+    """(GB/s, source): the measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        v = json.load(open(path)).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    return 6800.0, "fallback"
+
+
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -220,7 +236,7 @@ def cpu_oracle_rate(mats, ks, budget_s: float = 12.0, frac_rows: float | None = 
                 t_total += time.perf_counter() - t0
                 flops += 2.0 * nz * k
         sweeps += 1
-        if t_total >= budget_s or sweeps >= 50:
+        if t_total >= budget_s or sweeps >= 1000:
             break
     what = f"{sweeps} full sweep(s)" if frac_rows is None else f"{sweeps} sweep(s) over the first {frac_rows:.0%} of rows"
     return flops / t_total / 1e9, threads, f"{what} of the workload, {t_total:.1f} s timed on {threads} thread(s)"
@@ -293,11 +309,87 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------- GPU arm
 
 def launches_per_call(cfg: dict, k: int, dtype_vec: int = 2) -> int:
-    """Kernels one product call launches: ROWS 1 per column panel; MERGE partition is
-    precomputed by the plan, then kernel + carry fix-up per panel."""
+    """Kernels one product call launches: ROWS and ROWS_TMA 1 per column panel; MERGE partition
+    is precomputed by the plan, then kernel + carry fix-up per panel; a relabelling plan adds
+    the scatter of x into the relabelled order."""
     panel = 32 * dtype_vec if k > 1 else 1
     panels = (k + panel - 1) // panel
-    return panels * (1 if cfg["variant"] == 1 else 2)
+    return panels * (1 if cfg["variant"] in (1, 3) else 2) + (1 if cfg.get("relabel", 0) else 0)
+
+
+def measure_spmm(gbs, torch, dev, items, steps, warmup, ks=(4, 8, 16)):
+    """SpMM Y = A X (Sec. 5) at k in `ks` on the sweep's resident matrices, each product through
+    an autotuned plan, timed cold (256 MiB L2 flush before every product) with CUDA events."""
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hbm_peak = measured_hbm_peak()[0]
+    out = []
+    sampler = ClockSampler(gpu_smi_id(torch, dev.index or 0))
+    for it in items:
+        A = it["A"]
+        for k in ks:
+            X = torch.from_numpy(synth.uniform(A.n * k, seed=synth.BASE_SEED + 12, stream=k).reshape(A.n, k)).to(dev)
+            Y = torch.empty((A.m, k), dtype=torch.float64, device=dev)
+            plan = gbs.Plan(it["rp"], it["ci"], A.n, torch.float64, k, tune=True)
+            for _ in range(warmup):
+                plan.spmm(it["v"], X, Y)
+            torch.cuda.synchronize(dev)
+            if not sampler.rows:
+                sampler.start()
+                time.sleep(0.05)
+            evs = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                plan.spmm(it["v"], X, Y)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize(dev)
+            ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+            by = compulsory_bytes(A.m, A.n, A.nnz, k)
+            out.append({"matrix": it["name"], "k": k, "ms": ms, "flops": 2.0 * A.nnz * k, "bytes": by,
+                        "gflops": 2.0 * A.nnz * k / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm_peak,
+                        "config": plan.config})
+            del plan, X, Y
+    sampler.stop()
+    return {"products": out, "clocks": sampler.summary(), "steps": steps}
+
+
+def reduce_max(torch, dev, values, world):
+    """Element-wise maximum of a list of floats over the ranks."""
+    if world == 1 or not values:
+        return list(values)
+    import torch.distributed as dist
+
+    t = torch.tensor(values, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def host_numa_info(torch, dev_index: int) -> dict:
+    """Where the host side of the end-to-end copies lives: the CPUs this process may run on, and
+    the NUMA node of those CPUs and of the GPU's PCI function (Linux sysfs; empty where absent)."""
+    info = {}
+    try:
+        cpus = sorted(os.sched_getaffinity(0))
+        info["process_cpus"] = f"{cpus[0]}-{cpus[-1]} ({len(cpus)})" if cpus else ""
+        nodes = set()
+        for c in cpus:
+            for d in os.listdir(f"/sys/devices/system/cpu/cpu{c}"):
+                if d.startswith("node") and d[4:].isdigit():
+                    nodes.add(int(d[4:]))
+        info["process_cpu_numa_nodes"] = sorted(nodes)
+    except OSError:
+        pass
+    try:
+        p = torch.cuda.get_device_properties(dev_index)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as fh:
+            info["gpu_pci_numa_node"] = int(fh.read().strip())
+    except (OSError, ValueError, AttributeError):
+        pass
+    return info
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -465,20 +557,30 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
 
+    # ---- the host-to-device copy rate alone: the step's input copies from the same pinned
+    # buffers on the same copy stream, nothing else running (best of three passes)
+    h2d_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        hc0, hc1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hc0.record(h2d_stream)
+        with torch.cuda.stream(h2d_stream):
+            for it, hb in zip(items, pinned):
+                it["rp"].copy_(hb["rp"], non_blocking=True)
+                it["ci"].copy_(hb["ci"], non_blocking=True)
+                it["v"].copy_(hb["v"], non_blocking=True)
+                it["X"].copy_(hb["X"], non_blocking=True)
+        hc1.record(h2d_stream)
+        torch.cuda.synchronize(dev)
+        h2d_ms.append(hc0.elapsed_time(hc1))
+    h2d_gbs = h2d / (min(h2d_ms) * 1e-3) / 1e9
+    del pinned
+
     # ---- max over ranks
-    t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    step_ms_max, e2e_ms_max = reduce_max(torch, dev, [step_ms, e2e_ms], world)
 
     # ---- per-matrix report, dominant kernel roofline
-    hbm_peak = None
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path):
-        hbm_peak = json.load(open(peaks_path)).get("hbm_gbs")
-    peak_src = "measured"
-    if not hbm_peak:
-        hbm_peak, peak_src = 6800.0, "fallback"
+    hbm_peak, peak_src = measured_hbm_peak()
     # FP64 roof from the unit counts: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma
     # peak_sustained = 2), 2 flops each, at the median SM clock sampled during the timed region
     clk = sampler.summary()
@@ -519,15 +621,51 @@ def run_gpu(args, rank, world, local_rank):
                    "wall_s_timed_region": wall},
         "roofline": roofline,
         "e2e": {"value": world * flops_step / (e2e_ms_max * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps, "ms_per_step": e2e_ms_max,
+                "h2d_gbs_measured": h2d_gbs, "h2d_ms_alone": min(h2d_ms),
+                "h2d_bound_ms": h2d / (h2d_gbs * 1e9) * 1e3, "host": host_numa_info(torch, local_rank),
                 "note": "pinned host buffers; one untimed warm-up step; copies on their own streams overlap "
-                        "the products; host-to-device copies on this GPU peak near 211 GB/s"},
+                        "the products; h2d_gbs_measured = the step's input copies alone on the copy stream "
+                        "(best of three), so h2d_bound_ms is the floor the copies set on ms_per_step"},
         "clocks": sampler.summary(),
         "gpu_launches": launches,
         "fp64_peak_gflops_derived": fp64_peak_gflops, "fp64_probe_gflops": fp64_probe_gflops,
         "fp64_emulation": bool(args.emulate),
         "per_matrix": per,
     }
+    # ---- the rest of the metric on the same line: SpMM k = 4, 8, 16 on the sweep's matrices,
+    # the 512-matrix batch against its launch loops, and backward / forward on R-MAT 20
+    if args.workload == "spmv" and not args.sweep_only and not args.only and not args.config:
+        ksteps = max(3, min(args.steps, 20))
+        sp = measure_spmm(gbs, torch, dev, [it for it in items if it["k"] == 1], ksteps, args.warmup)
+        ms = reduce_max(torch, dev, [p["ms"] for p in sp["products"]], world)
+        for p, t_ in zip(sp["products"], ms):
+            p["ms"] = t_
+            p["gflops"] = p["flops"] / t_ / 1e6
+            p["hbm_frac"] = p["bytes"] / t_ / 1e6 / hbm_peak
+            p["fp64_frac"] = p["flops"] / t_ / 1e6 / fp64_peak_gflops
+        tot_ms = sum(p["ms"] for p in sp["products"])
+        line["spmm"] = {"gflops": world * sum(p["flops"] for p in sp["products"]) / (tot_ms * 1e-3) / 1e9,
+                        "workload": WORKLOAD_TEXT["spmm"].replace("k in {1,4,8,16}", "k in {4,8,16}"),
+                        "steps": sp["steps"], "l2": "256 MiB write before every product (untimed)",
+                        "clocks": sp["clocks"],
+                        "per_product": [{k_: v_ for k_, v_ in p.items() if k_ not in ("flops", "bytes")}
+                                        for p in sp["products"]]}
+        b = measure_batched(gbs, torch, dev, args, rank, world, ksteps, args.warmup)
+        b["ms"], b["looped_ms"], b["looped_tuned_ms"] = reduce_max(
+            torch, dev, [b["ms"], b["looped_ms"], b["looped_tuned_ms"]], world)
+        b["flops"], b["bytes"] = b["flops"] * world, b["bytes"] * world
+        line["batched"] = batched_report(b, world, hbm_peak, fp64_peak_gflops)
+        line["batched"]["workload"] = WORKLOAD_TEXT["batched"]
+        line["batched_vs_looped"] = line["batched"]["batched_vs_looped"]
+        line["batched_vs_looped_tuned"] = line["batched"]["batched_vs_looped_tuned"]
+        ag = measure_autograd(gbs, torch, dev, rank, ksteps, args.warmup)
+        fb = reduce_max(torch, dev, [v_ for r_ in ag["results"] for v_ in (r_["fwd_ms"], r_["bwd_ms"])], world)
+        for j, r_ in enumerate(ag["results"]):
+            r_["fwd_ms"], r_["bwd_ms"] = fb[2 * j], fb[2 * j + 1]
+            r_["bwd_over_fwd"] = r_["bwd_ms"] / r_["fwd_ms"]
+        line["autograd"] = dict(ag, workload=WORKLOAD_TEXT["autograd"])
+        line["bwd_over_fwd"] = {f"{r_['dtype']}_k{r_['k']}": r_["bwd_over_fwd"] for r_ in ag["results"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, what = cpu_oracle_rate(mats, ks)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": what}
@@ -555,25 +693,19 @@ def shard_for_rank(costs, world: int, rank: int):
     return [i for i in range(len(costs)) if owner[i] == rank]
 
 
-def run_batched(args, rank, world, local_rank):
-    import torch
-    import torch.distributed as dist
-
-    import paper_1302_1078_gb300 as gbs
-
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
+def measure_batched(gbs, torch, dev, args, rank, world, steps, warmup, shard=False, batch_size=512):
+    """The 512-matrix k = 8 batch (one persistent launch replayed from a CUDA graph) against
+    the per-matrix launch loops.  Returns the timings and ratios as a dict (per-rank times;
+    the caller reduces them across ranks)."""
     k = 8
-    if args.shard:
+    if shard:
         # one batch split across the ranks (strong scaling)
-        specs = synth.batch_specs(args.batch_size)
+        specs = synth.batch_specs(batch_size)
         costs = [sp.rows * (5 if sp.kind == "stencil2d" else sp.avg) for sp in specs]
         mine = shard_for_rank(costs, world, rank)
     else:
         # every rank its own independent batch (weak scaling)
-        specs = synth.batch_specs(args.batch_size, seed=synth.BASE_SEED + 4 + 1000 * rank)
+        specs = synth.batch_specs(batch_size, seed=synth.BASE_SEED + 4 + 1000 * rank)
         mine = list(range(len(specs)))
     mats, Xs, Ys, flops, bytes_ = [], [], [], 0.0, 0
     for i in mine:
@@ -587,16 +719,18 @@ def run_batched(args, rank, world, local_rank):
         Ys.append(torch.empty((A.m, k), dtype=torch.float64, device=dev))
         flops += 2.0 * A.nnz * k
         bytes_ += compulsory_bytes(A.m, A.n, A.nnz, k)
+    t_plan0 = time.perf_counter()
     plan = gbs.BatchedPlan(mats, Xs, Ys, tune=True)
+    t_plan = time.perf_counter() - t_plan0
     info = plan.info()
     # the baseline a per-matrix user would run: each matrix's own standalone-tuned configuration
     plan_pm = gbs.BatchedPlan(mats, Xs, Ys, tune=True, configs=[None] * len(mats))
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed(fn, steps):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for s_ in range(steps):
+    def timed(fn, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s_ in range(n):
             flush.zero_()
             evs[s_][0].record(stream)
             fn()
@@ -604,53 +738,81 @@ def run_batched(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         return [a.elapsed_time(b) for a, b in evs]
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.run()
         plan.run_looped()
         plan_pm.run_looped()
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(gpu_smi_id(torch, local_rank))
-    if world > 1:
-        dist.barrier()
+    sampler = ClockSampler(gpu_smi_id(torch, dev.index or 0))
     sampler.start()
     time.sleep(0.05)
-    torch.cuda.nvtx.range_push("timed")
-    t_batched = timed(plan.run, args.steps)
-    torch.cuda.nvtx.range_pop()
-    t_looped = timed(plan.run_looped, args.steps)
-    t_looped_pm = timed(plan_pm.run_looped, args.steps)
+    t_batched = timed(plan.run, steps)
+    t_looped = timed(plan.run_looped, steps)
+    t_looped_pm = timed(plan_pm.run_looped, steps)
     sampler.stop()
-    ms_b, ms_l, ms_lpm = statistics.mean(t_batched), statistics.mean(t_looped), statistics.mean(t_looped_pm)
-    t = torch.tensor([ms_b, ms_l, ms_lpm], dtype=torch.float64, device=dev)
-    tot = torch.tensor([flops, float(bytes_)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    ms_b, ms_l, ms_lpm = float(t[0]), float(t[1]), float(t[2])
-    flops_all, bytes_all = float(tot[0]), float(tot[1])
-    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     variants = {}
     for c in info["configs"]:
         key = "ROWS" if c["variant"] == 1 else "MERGE"
         variants[key] = variants.get(key, 0) + 1
+    ms_b, ms_l, ms_lpm = statistics.mean(t_batched), statistics.mean(t_looped), statistics.mean(t_looped_pm)
+    del plan, plan_pm, mats, Xs, Ys
+    return {"ms": ms_b, "looped_ms": ms_l, "looped_tuned_ms": ms_lpm, "flops": flops, "bytes": float(bytes_),
+            "matrices": len(mine), "grid": info["grid"], "work_items": info["total_items"], "variants": variants,
+            "plan_s": t_plan, "clocks": sampler.summary(), "steps": steps}
+
+
+def batched_report(r, world, hbm_peak, fp64_peak=None):
+    """Public fields of a batched measurement (after the cross-rank reduction)."""
+    out = {"ms": r["ms"], "gflops": r["flops"] / (r["ms"] * 1e-3) / 1e9,
+           "hbm_frac": r["bytes"] / (r["ms"] * 1e-3) / 1e9 / world / hbm_peak,
+           "batched_vs_looped": r["looped_ms"] / r["ms"], "looped_ms": r["looped_ms"],
+           "looped_gflops": r["flops"] / (r["looped_ms"] * 1e-3) / 1e9,
+           "batched_vs_looped_tuned": r["looped_tuned_ms"] / r["ms"], "looped_tuned_ms": r["looped_tuned_ms"],
+           "looped_note": "looped = the batch's own per-matrix configurations, one launch per matrix; "
+                          "looped_tuned = each matrix's standalone-tuned configuration, one launch per matrix",
+           "matrices_per_rank": r["matrices"], "grid": r["grid"], "work_items": r["work_items"],
+           "variants": r["variants"], "plan_build_s": r["plan_s"], "steps": r["steps"], "clocks": r["clocks"]}
+    if fp64_peak:
+        out["fp64_frac"] = r["flops"] / world / (r["ms"] * 1e-3) / 1e9 / fp64_peak
+    return out
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if world > 1:
+        dist.barrier()
+    r = measure_batched(gbs, torch, dev, args, rank, world, args.steps, args.warmup, shard=args.shard,
+                        batch_size=args.batch_size)
+    t = torch.tensor([r["ms"], r["looped_ms"], r["looped_tuned_ms"]], dtype=torch.float64, device=dev)
+    tot = torch.tensor([r["flops"], r["bytes"]], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    r["ms"], r["looped_ms"], r["looped_tuned_ms"] = float(t[0]), float(t[1]), float(t[2])
+    r["flops"], r["bytes"] = float(tot[0]), float(tot[1])
+    rep = batched_report(r, world, measured_hbm_peak()[0])
     line = {
-        "metric": METRIC, "value": flops_all / (ms_b * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "metric": METRIC, "value": rep["gflops"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
         "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT["batched"].replace("512", str(args.batch_size)),
-                   "matrices_per_rank": len(mine),
-                   "grid": info["grid"], "work_items": info["total_items"], "variants": variants,
-                   "l2": "256 MiB write before every step (untimed)"},
-        "batched_vs_looped": ms_l / ms_b, "looped_gflops": flops_all / (ms_l * 1e-3) / 1e9,
-        "looped_ms": ms_l,
-        "looped_note": "looped = the batch's own per-matrix configurations, one launch per matrix; "
-                       "looped_tuned = each matrix's standalone-tuned configuration, one launch per matrix",
-        "batched_vs_looped_tuned": ms_lpm / ms_b, "looped_tuned_ms": ms_lpm,
-        "roofline": {"bound": "hbm", "achieved": bytes_all / (ms_b * 1e-3) / 1e9 / world, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": bytes_all / (ms_b * 1e-3) / 1e9 / world / hbm_peak, "traffic": None,
+                   "matrices_per_rank": r["matrices"], "grid": r["grid"], "work_items": r["work_items"],
+                   "variants": r["variants"], "l2": "256 MiB write before every step (untimed)"},
+        "batched_vs_looped": rep["batched_vs_looped"], "looped_gflops": rep["looped_gflops"],
+        "looped_ms": r["looped_ms"], "looped_note": rep["looped_note"],
+        "batched_vs_looped_tuned": rep["batched_vs_looped_tuned"], "looped_tuned_ms": r["looped_tuned_ms"],
+        "roofline": {"bound": "hbm", "achieved": r["bytes"] / (r["ms"] * 1e-3) / 1e9 / world,
+                     "peak": measured_hbm_peak()[0], "unit": "GB/s", "frac": rep["hbm_frac"], "traffic": None,
                      "kernel": "batched_kernel (whole batch per launch)"},
-        "clocks": sampler.summary(),
+        "clocks": r["clocks"],
         "gpu_launches": args.steps,
     }
     if rank == 0:
@@ -748,8 +910,7 @@ def run_bcsr(args, rank, world, local_rank):
     shapes = {"rmat_s22_ef16": [(8, 1), (1, 8)]}  # larger blocks of a power-law matrix are mostly zeros
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    hbm_peak = measured_hbm_peak()[0]
 
     def timed_ms(fn):
         for _ in range(args.warmup):
@@ -809,13 +970,12 @@ def run_bcsr(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ autograd
 
-def run_autograd(args, rank, world, local_rank):
-    import torch
+def measure_autograd(gbs, torch, dev, rank, steps, warmup, dtypes=None):
+    """Forward Y = A X and backward (dX = A^T dY, dvals) on R-MAT scale 20, edge factor 16,
+    vals uniform[0.5, 1.5], k in {1, 8}; the transpose is built once and timed separately."""
+    import torch as _t
 
-    import paper_1302_1078_gb300 as gbs
-
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
+    dtypes = dtypes or (_t.float64, _t.float32)
     A = synth.rmat(20, ef=16, seed=synth.BASE_SEED + 3 + 1000 * rank, vals="u0.5_1.5")
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col_idx).to(dev)
@@ -827,8 +987,10 @@ def run_autograd(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     transpose_ms = e0.elapsed_time(e1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     results = []
-    for dtype in (torch.float64, torch.float32):
+    sampler = ClockSampler(gpu_smi_id(torch, dev.index or 0))
+    for dtype in dtypes:
         v = torch.from_numpy(A.vals).to(dev).to(dtype)
         for k in (1, 8):
             X = torch.from_numpy(synth.uniform(A.n * k, seed=5, stream=k)).to(dev).to(dtype)
@@ -836,20 +998,28 @@ def run_autograd(args, rank, world, local_rank):
             W = torch.rand((A.m,) if k == 1 else (A.m, k), dtype=dtype, device=dev)
             op.forward_raw(v, X)
             op.tplan.prepare(dtype, k, tune=True)  # tuned dX plan (one-time, like the forward plan)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 op.forward_raw(v, X)
                 op.tplan.backward(v, X, W)
             torch.cuda.synchronize(dev)
+            if not sampler.rows:
+                sampler.start()
+                time.sleep(0.05)
             fwd, bwd = [], []
-            for _ in range(args.steps):
-                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            for _ in range(steps):
+                # each pass starts cold, like the sweep's products: the forward after an L2 flush,
+                # the backward after another one
+                a, b, c, d = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+                flush.zero_()
                 a.record(stream)
                 op.forward_raw(v, X)
                 b.record(stream)
-                op.tplan.backward(v, X, W)
+                flush.zero_()
                 c.record(stream)
+                op.tplan.backward(v, X, W)
+                d.record(stream)
                 fwd.append((a, b))
-                bwd.append((b, c))
+                bwd.append((c, d))
             torch.cuda.synchronize(dev)
             f = statistics.mean(x.elapsed_time(y) for x, y in fwd)
             bw = statistics.mean(x.elapsed_time(y) for x, y in bwd)
@@ -857,13 +1027,28 @@ def run_autograd(args, rank, world, local_rank):
                             "bwd_over_fwd": bw / f, "fwd_gflops": 2.0 * A.nnz * k / (f * 1e-3) / 1e9,
                             "bwd_gflops": 4.0 * A.nnz * k / (bw * 1e-3) / 1e9,
                             "fwd_config": op.plan(dtype, k).config, "dX_config": op.tplan.config(dtype, k)})
-    main_r = results[0]
+    sampler.stop()
+    del op
+    return {"m": A.m, "nnz": A.nnz, "transpose_ms_one_time": transpose_ms, "results": results,
+            "clocks": sampler.summary(), "steps": steps,
+            "l2": "256 MiB write before the forward and again before the backward (untimed)"}
+
+
+def run_autograd(args, rank, world, local_rank):
+    import torch
+
+    import paper_1302_1078_gb300 as gbs
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    r = measure_autograd(gbs, torch, dev, rank, args.steps, args.warmup)
+    main_r = r["results"][0]
     line = {
         "metric": METRIC, "value": main_r["fwd_gflops"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main_r["fwd_ms"] + main_r["bwd_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT["autograd"], "m": A.m, "nnz": A.nnz},
-        "transpose_ms_one_time": transpose_ms, "autograd": results,
+        "config": {"workload": WORKLOAD_TEXT["autograd"], "m": r["m"], "nnz": r["nnz"], "l2": r["l2"]},
+        "transpose_ms_one_time": r["transpose_ms_one_time"], "autograd": r["results"], "clocks": r["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -878,6 +1063,8 @@ def main():
     ap.add_argument("--workload", default="spmv", choices=["spmv", "spmm", "small", "batched", "autograd", "rcm", "bcsr"])
     ap.add_argument("--impl", default="gbspmv", choices=["gbspmv", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="spmv: time only the SpMV sweep (no SpMM, batched or autograd sections)")
     ap.add_argument("--shard", action="store_true", help="batched: split one batch across ranks (strong scaling)")
     ap.add_argument("--config", default=None,
                     help='spmv/spmm: one fixed configuration for every product instead of the tuner\'s, as JSON '

@@ -97,6 +97,20 @@ typedef enum {
  *                Each such product is accurate to about 2^-44 of |a x| and the
  *                sums stay within 3e-13 of sum |a x| per entry; operands
  *                outside [2^-38, 2^39) in magnitude use the FP64 pipe.
+ *   relabel      plans only (0 elsewhere): the plan relabels the columns by
+ *                their number of stored entries, most first (ties by column
+ *                id), once, and every call first scatters x into that order
+ *                (x'[newid[j]] = x[j], or the rows of X) and multiplies with
+ *                the relabelled column ids.  The paper ties SpMV speed to the
+ *                reuse of x's cache lines (Sec. 4.1, Sec. 4.3) and reorders
+ *                matrices for it (Sec. 4.4); on a power-law matrix this packs
+ *                the most gathered entries of x into the fewest lines.  Rows
+ *                and the order of each row's terms are unchanged, so results
+ *                are bitwise those of relabel = 0.  1: relabel; h >= 2:
+ *                relabel, and the MERGE_DIRECT SpMV gathers columns at or
+ *                above h * 1024 without allocating them in L1.  The plan then
+ *                owns 4 * nnz + 4 * n bytes of relabelled indices and an
+ *                n x k copy of x / X.
  */
 typedef struct {
   int variant;
@@ -105,6 +119,7 @@ typedef struct {
   int tile_nnz;
   int items;
   int emul;
+  int relabel;
 } gbs_config;
 
 /* Row-length statistics computed on the device (gbs_csr_stats). */
@@ -333,6 +348,14 @@ int gbs_plan_destroy(gbs_plan* plan);
 int gbs_plan_get_config(const gbs_plan* plan, gbs_config* cfg);
 int gbs_plan_set_config(gbs_plan* plan, const gbs_config* cfg);
 int gbs_plan_get_stats(const gbs_plan* plan, gbs_stats* out);
+/*
+ * The column relabelling of a plan whose configuration has relabel != 0:
+ * newid[j] for the n columns (int32, device or host pointer), the rank of
+ * column j when the columns are ordered by stored entries, most first, ties
+ * by column id.  GBS_EINVAL if the plan does not relabel.  Synchronises
+ * `stream`.
+ */
+int gbs_plan_relabel_ids(const gbs_plan* plan, int* newid, void* stream);
 /* y <- A x (plan k must be 1) or Y <- A X (ldx, ldy >= plan k). */
 int spmv_csr_plan(const gbs_plan* plan, const void* vals, const void* x, void* y, void* stream);
 /*

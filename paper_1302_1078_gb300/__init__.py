@@ -329,6 +329,14 @@ class Plan:
         _capi.check(lib().gbs_plan_get_stats(self._h, ctypes.byref(st)), "gbs_plan_get_stats")
         return st.as_dict()
 
+    def relabel_ids(self, stream=None):
+        """newid (int32, n entries, on the device) of a plan whose configuration relabels its
+        columns: the rank of each column by stored entries, most first, ties by column id."""
+        out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _capi.check(lib().gbs_plan_relabel_ids(self._h, _ptr(out), _stream(self.device, stream)),
+                    "gbs_plan_relabel_ids")
+        return out
+
     def spmv(self, vals, x, y=None, stream=None):
         _need_cuda(vals, x, y)
         if y is None:

@@ -42,7 +42,8 @@ PLAN_EMULATE = 4
 
 
 class gbs_config(ctypes.Structure):
-    _fields_ = [("variant", I32), ("lanes", I32), ("threads", I32), ("tile_nnz", I32), ("items", I32), ("emul", I32)]
+    _fields_ = [("variant", I32), ("lanes", I32), ("threads", I32), ("tile_nnz", I32), ("items", I32), ("emul", I32),
+                ("relabel", I32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -77,6 +78,7 @@ SIGNATURES = {
     "gbs_plan_get_config": (I32, [P, ctypes.POINTER(gbs_config)]),
     "gbs_plan_set_config": (I32, [P, ctypes.POINTER(gbs_config)]),
     "gbs_plan_get_stats": (I32, [P, ctypes.POINTER(gbs_stats)]),
+    "gbs_plan_relabel_ids": (I32, [P, P, P]),
     "spmv_csr_plan": (I32, [P, P, P, P, P]),
     "gbs_plan_status": (I32, [P, ctypes.POINTER(I32), P]),
     "spmm_csr_plan": (I32, [P, P, P, I32, P, I32, P]),

@@ -117,6 +117,7 @@ int check_cfg(const gbs_config& c) {
     return fail(GBS_EINVAL, "tile_nnz must be in [32, 16384]");
   if (is_merge(c.variant) && (c.items < 0 || c.items > 256)) return fail(GBS_EINVAL, "items must be in [0, 256]");
   if (c.emul < 0 || c.emul > 3) return fail(GBS_EINVAL, "emul must be in [0, 3]");
+  if (c.relabel < 0 || c.relabel > 1024) return fail(GBS_EINVAL, "relabel must be in [0, 1024]");
   return GBS_OK;
 }
 
@@ -167,9 +168,13 @@ MergeGeom merge_geom(const gbs_config& cfg, int m, int nnz, int dtype, int k, bo
 // configuration.  Merge scratch comes from `mb` if given (plan), else from the stream-ordered
 // allocator.  `coords_ready`: the partition in mb is valid for this configuration.
 int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx, void* Y, long long ldy,
-                const gbs_config& cfg, MergeBuffers* mb, bool coords_ready, cudaStream_t s, int* status = nullptr) {
+                const gbs_config& cfg, MergeBuffers* mb, bool coords_ready, cudaStream_t s, int* status = nullptr,
+                int vec16_as = -1) {
   if (A.m == 0 || k == 0) return GBS_OK;
-  const bool vec16 = dense_vec16(dtype, k, X, ldx, Y, ldy);
+  // 128-bit column access when X, Y and their leading dimensions allow it; vec16_as (0 / 1)
+  // imposes the decision made for the caller's own operands (0 is always safe; 1 only for
+  // operands that allow it)
+  const bool vec16 = vec16_as >= 0 ? vec16_as != 0 : dense_vec16(dtype, k, X, ldx, Y, ldy);
   const int P = panel_cols(dtype, vec16);
   const size_t es = dsize(dtype);
   cudaError_t e = cudaSuccess;
@@ -615,6 +620,7 @@ static int product_entry(int m, int n, int nnz, const int* row_ptr, const int* c
   } else {
     c = *cfg;
   }
+  if (c.relabel != 0) return fail(GBS_EINVAL, "relabel needs a plan (gbs_plan_create / gbs_plan_set_config)");
   c = normalize(c, dtype);
   rc = check_cfg(c);
   if (rc) return rc;
@@ -658,18 +664,58 @@ struct gbs_plan {
   int* status = nullptr;  // device word: bounded-wait status of the pipelined variant
   const int* perm = nullptr;  // values read through this permutation (plans of A^T inside a transpose plan)
   float tuned_ms = 0.0f;      // the tuner's time of the chosen configuration (0: not tuned)
+  // column relabelling (cfg.relabel != 0): newid[n], col_rl[nnz] = newid[col_idx], and the
+  // relabelled copy of x / X (n rows of ldxp elements)
+  int* newid = nullptr;
+  int* col_rl = nullptr;
+  void* xbuf = nullptr;
+  long long ldxp = 1;
+  int col_max_deg = -1;  // column-degree statistics, computed on first need
+  double col_cv = 0.0;
+  bool tuning = false;   // the tuner is trying configurations: keep the relabelling between them
 };
 
 namespace {
 
 // Allocate (or free) the plan's merge scratch for its configuration and compute the
 // partition.  Scratch is sized for 128-bit column panels, the widest case.
+void relabel_release(gbs_plan* p) {
+  if (p->newid) cudaFree(p->newid);
+  if (p->col_rl) cudaFree(p->col_rl);
+  if (p->xbuf) cudaFree(p->xbuf);
+  p->newid = p->col_rl = nullptr;
+  p->xbuf = nullptr;
+}
+
+// The relabelled indices and x buffer of a plan whose configuration relabels (built once).
+int relabel_prepare(gbs_plan* p, cudaStream_t s) {
+  if (p->cfg.relabel == 0 || p->newid || p->n == 0) return GBS_OK;
+  const size_t es = dsize(p->dtype);
+  const int v = (int)(16 / es);
+  p->ldxp = p->k == 1 ? 1 : (long long)((p->k + v - 1) / v) * v;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->newid), sizeof(int) * (size_t)p->n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->col_rl), sizeof(int) * (size_t)std::max(p->nnz, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->xbuf, es * (size_t)p->n * (size_t)p->ldxp);
+  if (e == cudaSuccess) e = relabel_build(p->n, p->nnz, p->col_idx, p->newid, p->col_rl, s);
+  if (e != cudaSuccess) {
+    relabel_release(p);
+    return cuda_fail(e, "column relabelling");
+  }
+  return GBS_OK;
+}
+
 int plan_prepare(gbs_plan* p, cudaStream_t s) {
   if (p->mb.base) {
     cudaFree(p->mb.base);
     p->mb = MergeBuffers{};
   }
   p->coords_ready = false;
+  if (p->cfg.relabel == 0) {
+    if (!p->tuning) relabel_release(p);
+  } else {
+    const int rc = relabel_prepare(p, s);
+    if (rc) return rc;
+  }
   if (p->cfg.variant == GBS_VARIANT_ROWS_TMA && p->m > 0) {
     // the tile must hold the largest row block: measure it on the device
     int lanes = p->cfg.lanes;
@@ -710,15 +756,28 @@ int plan_prepare(gbs_plan* p, cudaStream_t s) {
 
 int plan_run(const gbs_plan* p, const void* vals, const void* X, long long ldx, void* Y, long long ldy, cudaStream_t s) {
   CsrView A{p->m, p->n, p->nnz, p->row_ptr, p->col_idx, vals, p->perm};
+  // the caller's operands decide the column access (and with it the merge geometry), also when
+  // the product reads the relabelled copy of X, so that relabelling never changes a result
+  const bool vec16 = dense_vec16(p->dtype, p->k, X, ldx, Y, ldy);
+  if (p->cfg.relabel != 0 && p->newid && p->m > 0 && p->k > 0) {
+    // x' = x in the relabelled column order, then the product with the relabelled column ids
+    const bool src16 = p->k > 1 && aligned16(X) && (ldx * (long long)dsize(p->dtype)) % 16 == 0;
+    cudaError_t e = relabel_dense(p->dtype, p->n, p->k, X, ldx, p->newid, p->xbuf, p->ldxp, src16, s);
+    if (e != cudaSuccess) return cuda_fail(e, "relabel of x");
+    A.col_idx = p->col_rl;
+    if (p->cfg.relabel >= 2) A.hot_cols = (int)std::min<long long>(INT_MAX - 1, (long long)p->cfg.relabel * 1024);
+    X = p->xbuf;
+    ldx = p->ldxp;
+  }
+  const int as = vec16 ? 1 : 0;
   if (is_merge(p->cfg.variant)) {
     // the partition was made for 128-bit column access; if this call cannot use it the
     // lane count differs and the stream-ordered path is used instead
-    const bool vec16 = dense_vec16(p->dtype, p->k, X, ldx, Y, ldy);
-    if (p->k > 1 && !vec16) return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s);
+    if (p->k > 1 && !vec16) return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s, nullptr, as);
     MergeBuffers mb = p->mb;
-    return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, &mb, p->coords_ready, s);
+    return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, &mb, p->coords_ready, s, nullptr, as);
   }
-  return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s, p->status);
+  return run_product(A, p->dtype, p->k, X, ldx, Y, ldy, p->cfg, nullptr, false, s, p->status, as);
 }
 
 // Candidate configurations for the tuner.
@@ -781,6 +840,23 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
     add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, 0);
   }
+  // skewed column degrees (a power-law matrix): the merge forms again on columns relabelled
+  // hottest first, with every gather through L1 or with the cold ones bypassing it
+  const double mean_col = p->n > 0 ? (double)p->nnz / p->n : 0.0;
+  if (p->col_max_deg > 16.0 * mean_col + 256.0 || p->col_cv > 2.0) {
+    std::vector<gbs_config> rl;
+    for (const gbs_config& g : c)
+      if (is_merge(g.variant) && g.emul == 0) {
+        rl.push_back(g);
+        rl.back().relabel = 1;
+        if (p->k == 1 && g.variant == GBS_VARIANT_MERGE_DIRECT && g.threads == 256 && g.items <= 23)
+          for (int h : {8, 16, 24}) {
+            rl.push_back(g);
+            rl.back().relabel = h;
+          }
+      }
+    c.insert(c.end(), rl.begin(), rl.end());
+  }
   if (p->perm) {
     // values through a permutation: the variants that support it
     std::vector<gbs_config> keep;
@@ -826,6 +902,14 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
   const long long ldx = p->k == 1 ? 1 : ldp;
   float best = 1e30f;
   gbs_config best_cfg = p->cfg;
+  if (rc == GBS_OK && p->col_max_deg < 0) {
+    if (col_degree_stats(p->n, p->nnz, p->col_idx, &p->col_max_deg, &p->col_cv, s) != cudaSuccess) {
+      p->col_max_deg = 0;  // statistics unavailable: no relabelled candidates
+      p->col_cv = 0.0;
+      cudaGetLastError();
+    }
+  }
+  p->tuning = true;
   if (rc == GBS_OK) {
     for (const gbs_config& c : tune_candidates(p)) {
       if (check_cfg(c) != GBS_OK) continue;
@@ -847,8 +931,9 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
       if (!ok) continue;
       std::sort(times, times + kReps);
       if (tune_log())
-        std::fprintf(stderr, "gbspmv tune m=%d nnz=%d k=%d: variant=%d lanes=%d threads=%d tile=%d items=%d emul=%d -> %.4f ms\n",
-                     p->m, p->nnz, p->k, c.variant, c.lanes, c.threads, p->cfg.tile_nnz, c.items, c.emul, times[kReps / 2]);
+        std::fprintf(stderr, "gbspmv tune m=%d nnz=%d k=%d: variant=%d lanes=%d threads=%d tile=%d items=%d emul=%d "
+                     "relabel=%d -> %.4f ms\n", p->m, p->nnz, p->k, c.variant, c.lanes, c.threads, p->cfg.tile_nnz,
+                     c.items, c.emul, c.relabel, times[kReps / 2]);
       if (times[kReps / 2] < best) {
         best = times[kReps / 2];
         best_cfg = c;
@@ -856,8 +941,10 @@ int plan_tune(gbs_plan* p, cudaStream_t s) {
     }
     p->cfg = best_cfg;
     p->tuned_ms = best < 1e30f ? best : 0.0f;
+    p->tuning = false;
     rc = plan_prepare(p, s);
   }
+  p->tuning = false;
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   cudaFree(vals);
@@ -911,6 +998,7 @@ int plan_create_impl(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr,
     rc = (flags & GBS_PLAN_TUNE) && m > 0 ? plan_tune(p, s) : plan_prepare(p, s);
   }
   if (rc != GBS_OK) {
+    relabel_release(p);
     if (p->mb.base) cudaFree(p->mb.base);
     cudaFree(p->status);
     delete p;
@@ -931,6 +1019,7 @@ int gbs_plan_create(gbs_plan** plan, int m, int n, int nnz, const int* row_ptr, 
 
 int gbs_plan_destroy(gbs_plan* plan) {
   if (!plan) return GBS_OK;
+  relabel_release(plan);
   if (plan->mb.base) cudaFree(plan->mb.base);
   if (plan->status) cudaFree(plan->status);
   delete plan;
@@ -956,6 +1045,16 @@ int gbs_plan_get_stats(const gbs_plan* plan, gbs_stats* out) {
   if (!plan || !out) return fail(GBS_EINVAL, "NULL pointer");
   *out = plan->stats;
   return GBS_OK;
+}
+
+int gbs_plan_relabel_ids(const gbs_plan* plan, int* newid, void* stream) {
+  if (!plan || (!newid && plan->n > 0)) return fail(GBS_EINVAL, "NULL pointer");
+  if (plan->cfg.relabel == 0 || (!plan->newid && plan->n > 0)) return fail(GBS_EINVAL, "the plan does not relabel");
+  if (plan->n == 0) return GBS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(newid, plan->newid, sizeof(int) * (size_t)plan->n, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "relabel export");
 }
 
 int gbs_plan_set_config(gbs_plan* plan, const gbs_config* cfg) {
@@ -1613,6 +1712,8 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
       int rc = GBS_OK;
       if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE) {
         rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": batched configurations are ROWS or MERGE");
+      } else if (g.relabel != 0) {
+        rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": column relabelling is for plans of one matrix");
       } else {
         g.threads = kBatchThreads;
         g.emul = 0;

@@ -79,6 +79,18 @@ __device__ __forceinline__ float ld_keep(const float* ptr, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(ptr), "l"(pol));
   return r;
 }
+// The same gathers without L1 allocation: for the entries of x that are rarely reused (the cold
+// columns of a relabelled matrix), so that they do not evict the hot ones from L1.
+__device__ __forceinline__ double ld_keep_na(const double* ptr, uint64_t pol) {
+  double r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(ptr), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float ld_keep_na(const float* ptr, uint64_t pol) {
+  float r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(ptr), "l"(pol));
+  return r;
+}
 __device__ __forceinline__ double2 ld_keep_v2(const double* ptr, uint64_t pol) {
   double2 r;
   asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(ptr), "l"(pol));

@@ -11,6 +11,8 @@ struct CsrView {
   const int* col_idx;
   const void* vals;
   const int* perm = nullptr;  // if set, the value of entry p is vals[perm[p]] (ROWS, MERGE, MERGE_DIRECT)
+  int hot_cols = 0;           // > 0: columns relabelled hottest first; MERGE_DIRECT SpMV gathers
+                              // columns >= hot_cols without L1 allocation
 };
 
 struct DenseView {
@@ -76,6 +78,21 @@ cudaError_t transpose_run(int m, int n, int nnz, const int* row_ptr, const int* 
                           int* scan_ws, cudaStream_t s);
 size_t transpose_hist_ints(int nnz);
 size_t transpose_scan_ws_ints(int nnz);
+// Stable LSD radix sort of n (key >= 0, value) pairs by the keys' low `bits` bits (transpose.cu);
+// hist / scan_ws sized as for a transpose of n nonzeros.
+cudaError_t radix_sort_pairs(int n, int bits, int* keys_a, int* keys_b, int* vals_a, int* vals_b, int* hist,
+                             int* scan_ws, int** keys_out, int** vals_out, cudaStream_t s);
+
+// Column relabelling by in-degree, hottest first (relabel.cu).  col_degree_stats: the largest
+// column degree and the coefficient of variation of the degrees (synchronises s).  relabel_build:
+// newid[n] (rank of each column) and col_rl[nnz] = newid[col_idx] (synchronises s).
+// relabel_dense: X'[newid[j], :] = X[j, :] for the n rows of X (k columns; vec16: X, X' and both
+// leading dimensions 16-byte aligned).
+cudaError_t col_degree_stats(int n, int nnz, const int* col_idx, int* max_deg, double* cv_deg, cudaStream_t s);
+cudaError_t relabel_build(int n, int nnz, const int* col_idx, int* newid, int* col_rl, cudaStream_t s);
+cudaError_t relabel_dense(int dtype, int n, int k, const void* X, long long ldx, const int* newid, void* Xp,
+                          long long ldxp, bool vec16, cudaStream_t s);
+
 // out[q] = src[perm[q]] for values of `dtype`.
 cudaError_t gather_values(int dtype, const void* src, const int* perm, int nnz, void* out, cudaStream_t s);
 

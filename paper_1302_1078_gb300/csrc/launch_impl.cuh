@@ -141,9 +141,9 @@ cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, b
   }
 }
 
-template <typename T, int VEC, int G, bool DIRECT, bool PERM>
+template <typename T, int VEC, int G, bool DIRECT, bool PERM, bool HOT = false>
 static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
-  auto kern = merge_kernel<T, VEC, G, DIRECT, PERM>;
+  auto kern = merge_kernel<T, VEC, G, DIRECT, PERM, HOT>;
   const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -159,6 +159,9 @@ static cudaError_t merge_g(const MergeArgs<T>& a, bool vec16, bool direct, int t
   constexpr int V = 16 / (int)sizeof(T);
   if (direct) {
     if (vec16 && a.k > 1) return merge_go<T, V, G, true, PERM>(a, threads, s);
+    if constexpr (G == 1) {
+      if (a.hot_cols < 0x7fffffff) return merge_go<T, 1, 1, true, PERM, true>(a, threads, s);
+    }
     return merge_go<T, 1, G, true, PERM>(a, threads, s);
   }
   if (vec16 && a.k > 1) return merge_go<T, V, G, false, PERM>(a, threads, s);
@@ -190,6 +193,7 @@ cudaError_t launch_merge_t(const CsrView& A, const DenseView& D, int g, bool vec
   a.aligned_vals = (reinterpret_cast<uintptr_t>(PERM ? static_cast<const void*>(A.perm) : A.vals) & 15) == 0;
   a.aligned_cols = (reinterpret_cast<uintptr_t>(A.col_idx) & 15) == 0;
   a.vals32 = !PERM && (reinterpret_cast<uintptr_t>(A.vals) & 31) == 0;
+  a.hot_cols = A.hot_cols > 0 ? A.hot_cols : 0x7fffffff;
   switch (g) {
     case 1: return merge_g<T, 1, PERM>(a, vec16, direct, threads, s);
     case 2: return merge_g<T, 2, PERM>(a, vec16, direct, threads, s);

@@ -35,6 +35,10 @@
 //     only the carry scan's few KB and L1 keeps the rest of the SM's 256 KB
 //     for the gathered x (on a power-law matrix the hot columns of x are what
 //     L1 can hold, and more of them stay there the larger L1 is).
+//   * HOT (direct form, one column): the matrix's columns were relabelled
+//     hottest first (relabel.cu), so the x entries below `hot_cols` are the
+//     ones gathered most often.  Gathers of columns at or above it skip L1,
+//     so that the rarely reused lines do not evict the hot head of x.
 //   * PERM: the value of stored entry p is vals[perm[p]], so the backward
 //     pass can run A^T on A's values without a permuted copy.  The staged
 //     form gathers the tile's values into shared memory (perm read with
@@ -69,6 +73,7 @@ struct MergeArgs {
   bool aligned_vals, aligned_cols;  // aligned_vals: perm when PERM
   bool vals32 = false;              // vals 32-byte aligned: a group of four doubles is one 256-bit load
   const int* __restrict__ perm = nullptr;  // PERM: value of entry p is vals[perm[p]]
+  int hot_cols = 0x7fffffff;               // HOT: columns below this are gathered through L1
 };
 
 // Merge-path search: split diagonal d of the (row ends x nonzeros) grid.
@@ -102,8 +107,9 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
 
 // One merge-path tile b of the product (the whole CTA works on it).  Used by the
 // standalone kernel below and by the batched persistent kernel.
-template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false>
+template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false, bool HOT = false>
 __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
+  static_assert(!HOT || (DIRECT && VEC == 1), "the hot-column policy is for the direct form's scalar gathers");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = blockDim.x / G;
   const int nw = blockDim.x / 32;
@@ -224,7 +230,10 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     // scalar up to a multiple of 4, then aligned 128-bit groups of four, then the tail
     auto gather = [&](int c) {
       Vec<T, VEC> xv;
-      if (col_full) {
+      if constexpr (HOT) {
+        xv.v[0] = c < a.hot_cols ? ld_keep(Xc + (long long)c * a.ldx, pol_keep)
+                                 : ld_keep_na(Xc + (long long)c * a.ldx, pol_keep);
+      } else if (col_full) {
         xv = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
       } else {
 #pragma unroll
@@ -428,9 +437,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   }
 }
 
-template <typename T, int VEC, int G, bool DIRECT, bool PERM = false>
+template <typename T, int VEC, int G, bool DIRECT, bool PERM = false, bool HOT = false>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
-  merge_tile<T, VEC, G, DIRECT, PERM>(a, blockIdx.x);
+  merge_tile<T, VEC, G, DIRECT, PERM, HOT>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of

@@ -136,6 +136,32 @@ static int grid_for(long long work, int threads = 256) {
   return (int)std::min<long long>(152LL * 32, std::max<long long>(1, (work + threads - 1) / threads));
 }
 
+// Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the keys, 8-bit digits
+// per pass; keys must be non-negative.  Input in keys_a / vals_a, keys_b / vals_b are the other
+// half of the ping-pong; *keys_out / *vals_out point at whichever pair holds the result.  hist and
+// scan_ws as for the transpose (transpose_hist_ints(n), transpose_scan_ws_ints(n) ints).
+cudaError_t radix_sort_pairs(int n, int bits, int* keys_a, int* keys_b, int* vals_a, int* vals_b, int* hist,
+                             int* scan_ws, int** keys_out, int** vals_out, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  int *ki = keys_a, *ko = keys_b, *vi = vals_a, *vo = vals_b;
+  if (n > 0) {
+    const int ntiles = (n + kSortTile - 1) / kSortTile;
+    const long long hcount = 256LL * ntiles;
+    for (int shift = 0; shift < bits; shift += 8) {
+      radix_upsweep<<<ntiles, kSortThreads, 0, s>>>(ki, n, shift, ntiles, hist);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = exclusive_scan_i32(hist, hist, hcount, scan_ws, s)) != cudaSuccess) return e;
+      radix_downsweep<<<ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, hist);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      std::swap(ki, ko);
+      std::swap(vi, vo);
+    }
+  }
+  *keys_out = ki;
+  *vals_out = vi;
+  return e;
+}
+
 // Transpose with caller-provided device buffers (see tplan_create for sizes).
 // Returns a CUDA error.  tmp must hold 2 * nnz + 2 * nnz ints + hist + scan workspace.
 cudaError_t transpose_run(int m, int n, int nnz, const int* row_ptr, const int* col_idx, int* rptrT, int* colT,
@@ -156,18 +182,9 @@ cudaError_t transpose_run(int m, int n, int nnz, const int* row_ptr, const int* 
     return e;
   int bits = 0;
   while (bits < 31 && (1LL << bits) < (long long)n) ++bits;
-  const int ntiles = (nnz + kSortTile - 1) / kSortTile;
-  const long long hcount = 256LL * ntiles;
-  int *ki = keys_a, *ko = keys_b, *vi = vals_a, *vo = vals_b;
-  for (int shift = 0; shift < bits; shift += 8) {
-    radix_upsweep<<<ntiles, kSortThreads, 0, s>>>(ki, nnz, shift, ntiles, hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan_i32(hist, hist, hcount, scan_ws, s)) != cudaSuccess) return e;
-    radix_downsweep<<<ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, nnz, shift, ntiles, hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    std::swap(ki, ko);
-    std::swap(vi, vo);
-  }
+  int *ki = nullptr, *vi = nullptr;
+  if ((e = radix_sort_pairs(nnz, bits, keys_a, keys_b, vals_a, vals_b, hist, scan_ws, &ki, &vi, s)) != cudaSuccess)
+    return e;
   // ki: sorted column ids, vi: original positions
   boundaries_kernel<<<grid_for((long long)nnz + 1), 256, 0, s>>>(ki, nnz, n, rptrT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -310,6 +310,86 @@ def test_checked_mode_refuses_a_bad_structure_before_the_product(gbs, monkeypatc
         gbs.Plan(rp, bad, A.n, torch.float64, 1, check=True)
     assert e.value.status == _capi.GBS_EINDEX
 
+# ------------------------------------------------- column relabelling (plans)
+
+RELABEL_BASES = [dict(variant=4, items=11), dict(variant=4, items=7, threads=128), dict(variant=2, items=15),
+                 dict(variant=1, lanes=2), dict(variant=3, lanes=4, threads=128)]
+
+
+def _relabel_run(plan, v, X, k):
+    return plan.spmv(v, X) if k == 1 else plan.spmm(v, X)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("name", ["rmat_14", "hub", "random_rect", "random_dup_unsorted", "empty_nnz", "one_row"])
+def test_relabelled_plan_is_bitwise_the_plain_plan(gbs, name, k, dtype):
+    """Relabelling the columns hottest first changes neither the rows nor the order of any row's
+    terms: every variant gives bitwise the result it gives without relabelling (including the
+    MERGE_DIRECT walk whose cold gathers skip L1), within the bound of the oracle; the relabelling
+    itself equals the oracle's bit for bit."""
+    A = matrix(name)
+    rp, ci, v = dev_csr(A, dtype)
+    if k == 1:
+        x = synth.uniform(A.n, seed=21).astype(NP[dtype])
+        Y_ref, R = oracle.spmv(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), x)
+        X = torch.from_numpy(x).cuda()
+    else:
+        ld = k + 1  # a row stride > k: the scatter of X's rows reads narrow rows
+        Xw = synth.uniform(A.n * ld, seed=22, stream=k).reshape(A.n, ld).astype(NP[dtype])
+        Y_ref, R = oracle.spmm(A.m, A.row_ptr, A.col_idx, A.vals.astype(NP[dtype]), Xw[:, :k])
+        X = torch.from_numpy(Xw).cuda()[:, :k]
+    want_ids = oracle.degree_relabel(A.n, A.col_idx)
+    for base in RELABEL_BASES:
+        try:
+            plan = gbs.Plan(rp, ci, A.n, dtype, k, config=base)
+        except gbs.GbsError as e:
+            # the pipelined variant refuses row blocks larger than its shared-memory tile (the
+            # hub rows of these power-law matrices); the refusal comes before any product
+            assert base["variant"] == 3 and e.status == -8, (base, e)
+            continue
+        y0 = _relabel_run(plan, v, X, k).clone()
+        assert_close(y0, Y_ref, R, dtype, f"{name} {base}")
+        for rl in (1, 8, 1024):
+            plan.set_config(dict(base, relabel=rl))
+            y1 = _relabel_run(plan, v, X, k)
+            assert torch.equal(y0, y1), f"{name} k={k} {base} relabel={rl}: not bitwise the plain result"
+            y2 = _relabel_run(plan, v, X, k)  # the relabelled copy of x is rebuilt on every call
+            assert torch.equal(y1, y2)
+        ids = plan.relabel_ids().cpu().numpy()
+        assert np.array_equal(ids, want_ids), f"{name}: relabelling differs from the oracle's"
+
+
+def test_relabel_is_plans_only(gbs):
+    A = matrix("rmat_14")
+    rp, ci, v = dev_csr(A)
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(gbs.GbsError):
+        gbs.spmv_csr(rp, ci, v, x, config=dict(variant=4, relabel=1))
+    plan = gbs.Plan(rp, ci, A.n, torch.float64, 1, config=dict(variant=4))
+    with pytest.raises(gbs.GbsError):
+        plan.relabel_ids()  # this plan does not relabel
+
+
+def test_relabelled_backward_is_bitwise_the_plain_one(gbs):
+    """dX = A^T dY through a relabelled plan of A^T (its columns are A's rows) equals the plain
+    plan's bit for bit."""
+    A = matrix("rmat_14")
+    rp, ci, v = dev_csr(A)
+    t = gbs.TransposePlan(rp, ci, A.n)
+    for k in (1, 8):
+        X = torch.from_numpy(synth.uniform(A.n * k, seed=23).reshape(A.n, k) if k > 1 else
+                             synth.uniform(A.n, seed=23)).cuda()
+        dY = torch.from_numpy(synth.uniform(A.m * k, seed=24).reshape(A.m, k) if k > 1 else
+                              synth.uniform(A.m, seed=24)).cuda()
+        t.set_config(torch.float64, k, dict(variant=4, items=11))
+        dX0, dv0 = t.backward(v, X, dY)
+        for rl in (1, 8):
+            t.set_config(torch.float64, k, dict(variant=4, items=11, relabel=rl))
+            dX1, dv1 = t.backward(v, X, dY)
+            assert torch.equal(dX0, dX1) and torch.equal(dv0, dv1), (k, rl)
+
+
 # ------------------------------------------------ full-size configurations
 
 FULL = {
@@ -331,6 +411,15 @@ def test_full_size_spmv_tuned_plan(gbs, name):
     assert_close(y, y_ref, r, torch.float64, f"{name} {plan.config}")
     y2 = gbs.spmv_csr(rp, ci, v, torch.from_numpy(x).cuda())
     assert_close(y2, y_ref, r, torch.float64, f"{name} auto")
+    cfg = plan.config
+    if cfg["relabel"]:
+        # the tuner's relabelled configuration is bitwise its plain counterpart, and the
+        # relabelling equals the oracle's
+        ids = plan.relabel_ids().cpu().numpy()
+        assert np.array_equal(ids, oracle.degree_relabel(A.n, A.col_idx))
+        plan.set_config(dict(cfg, relabel=0))
+        y3 = plan.spmv(v, torch.from_numpy(x).cuda())
+        assert torch.equal(y, y3), f"{name} {cfg}: relabelled result differs from the plain one"
 
 
 
