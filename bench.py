@@ -1005,11 +1005,11 @@ def measure_autograd(gbs, torch, dev, rank, steps, warmup, dtypes=None):
             if not sampler.rows:
                 sampler.start()
                 time.sleep(0.05)
-            fwd, bwd = [], []
+            fwd, bwd, bdx, bdv = [], [], [], []
             for _ in range(steps):
                 # each pass starts cold, like the sweep's products: the forward after an L2 flush,
-                # the backward after another one
-                a, b, c, d = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+                # the backward after another one; the backward's two parts are also timed alone
+                a, b, c, d, e, f_, g, h = (torch.cuda.Event(enable_timing=True) for _ in range(8))
                 flush.zero_()
                 a.record(stream)
                 op.forward_raw(v, X)
@@ -1018,12 +1018,24 @@ def measure_autograd(gbs, torch, dev, rank, steps, warmup, dtypes=None):
                 c.record(stream)
                 op.tplan.backward(v, X, W)
                 d.record(stream)
+                flush.zero_()
+                e.record(stream)
+                op.tplan.backward(v, X, W, need_dvals=False)
+                f_.record(stream)
+                flush.zero_()
+                g.record(stream)
+                op.tplan.backward(v, X, W, need_dX=False)
+                h.record(stream)
                 fwd.append((a, b))
                 bwd.append((c, d))
+                bdx.append((e, f_))
+                bdv.append((g, h))
             torch.cuda.synchronize(dev)
             f = statistics.mean(x.elapsed_time(y) for x, y in fwd)
             bw = statistics.mean(x.elapsed_time(y) for x, y in bwd)
             results.append({"dtype": str(dtype).replace("torch.", ""), "k": k, "fwd_ms": f, "bwd_ms": bw,
+                            "bwd_dX_alone_ms": statistics.mean(x.elapsed_time(y) for x, y in bdx),
+                            "bwd_dvals_alone_ms": statistics.mean(x.elapsed_time(y) for x, y in bdv),
                             "bwd_over_fwd": bw / f, "fwd_gflops": 2.0 * A.nnz * k / (f * 1e-3) / 1e9,
                             "bwd_gflops": 4.0 * A.nnz * k / (bw * 1e-3) / 1e9,
                             "fwd_config": op.plan(dtype, k).config, "dX_config": op.tplan.config(dtype, k)})

@@ -377,8 +377,10 @@ int spmm_csr_plan(const gbs_plan* plan, const void* vals, const void* X, int ldx
  *   A of each entry of A^T) and the row of every nonzero of A (the dvals
  *   pass); plus, only if a configuration that permutes the values first is
  *   chosen, nnz doubles of scratch.
- * It does not keep row_ptr / col_idx.  Synchronises `stream`.
- * The transpose is the one-time set-up of the backward pass.
+ * It does not keep row_ptr / col_idx.  It also creates a non-blocking
+ * stream and two events on the current device (spmv_csr_backward).
+ * Synchronises `stream`.  The transpose is the one-time set-up of the
+ * backward pass.
  */
 typedef struct gbs_tplan gbs_tplan;
 
@@ -423,6 +425,13 @@ int gbs_tplan_get_config(const gbs_tplan* plan, int dtype, int k, gbs_config* cf
  * calls that share such a plan must be ordered on one stream); dvals sums
  * each nonzero's k products in column order.  `plan` must come from
  * gbs_transpose_plan on the same (row_ptr, col_idx); row_ptr is unused.
+ * When both dX and dvals are asked for, the dvals pass runs on a stream the
+ * plan owns, concurrently with dX: it waits for the work enqueued on
+ * `stream` before the call, and `stream` waits for it before anything
+ * enqueued after the call (an event each way, which stream capture
+ * follows), so the call is ordered on `stream` like any other.  The plan's
+ * events are reused by every call: calls that share a plan must be issued
+ * from one host thread at a time.
  */
 int spmv_csr_backward(gbs_tplan* plan, const int* row_ptr, const int* col_idx, const void* vals, int dtype,
                       int k, const void* X, int ldx, const void* dY, int lddy, void* dX, int lddx, void* dvals,

@@ -1100,6 +1100,10 @@ struct gbs_tplan {
     bool gather;
   };
   std::vector<Prepared> plans;  // one per (dtype, k), made by gbs_tplan_prepare
+  // the dvals pass runs on this plan-owned stream, forked from and joined back into the
+  // caller's stream, concurrently with the dX product
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -1206,9 +1210,14 @@ int gbs_transpose_plan(gbs_tplan** out, int m, int n, int nnz, const int* row_pt
     return cuda_fail(e, "transpose");
   }
   rc = compute_stats(n, m, nnz, t->rptrT, &t->statsT, s);
+  if (rc == GBS_OK) {
+    e = cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_fail(e, "backward stream and events");
+  }
   if (rc) {
-    cudaFree(t->base);
-    delete t;
+    gbs_tplan_destroy(t);
     return rc;
   }
   *out = t;
@@ -1237,6 +1246,9 @@ int gbs_tplan_export(const gbs_tplan* t, int* rowptrT, int* colT, int* perm, voi
 
 int gbs_tplan_destroy(gbs_tplan* t) {
   if (!t) return GBS_OK;
+  if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+  if (t->ev_join) cudaEventDestroy(t->ev_join);
+  if (t->side) cudaStreamDestroy(t->side);
   for (auto& pp : t->plans) gbs_plan_destroy(pp.plan);
   if (t->valsT) cudaFree(t->valsT);
   if (t->base) cudaFree(t->base);
@@ -1327,6 +1339,18 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
   (void)row_ptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
+  // both outputs: the dvals pass runs on the plan's side stream while dX runs on `stream`; the
+  // two read the same inputs and write different outputs, and `stream` waits for the side
+  // stream before anything after this call
+  const bool fork = dX && dvals && t->nnz > 0 && t->side;
+  if (fork) {
+    e = cudaEventRecord(t->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t->side, t->ev_fork, 0);
+    if (e == cudaSuccess)
+      e = launch_sddmm(dtype, t->nnz, k, t->rows, col_idx, X, k == 1 ? 1 : ldx, dY, k == 1 ? 1 : lddy, dvals, t->side);
+    if (e == cudaSuccess) e = cudaEventRecord(t->ev_join, t->side);
+    if (e != cudaSuccess) return cuda_fail(e, "SDDMM launch (side stream)");
+  }
   if (dX) {
     // dX = A^T dY on the precomputed transpose
     const gbs_tplan::Prepared* prepared = nullptr;
@@ -1346,9 +1370,15 @@ int spmv_csr_backward(gbs_tplan* t, const int* row_ptr, const int* col_idx, cons
       if (c.variant == GBS_VARIANT_MERGE) c.variant = GBS_VARIANT_MERGE_DIRECT;
       rc = run_product(AT, dtype, k, dY, k == 1 ? 1 : lddy, dX, k == 1 ? 1 : lddx, c, nullptr, false, s);
     }
-    if (rc) return rc;
+    if (rc) {
+      if (fork) cudaStreamWaitEvent(s, t->ev_join, 0);  // never leave the side stream unjoined
+      return rc;
+    }
   }
-  if (dvals) {
+  if (fork) {
+    e = cudaStreamWaitEvent(s, t->ev_join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "join of the side stream");
+  } else if (dvals) {
     e = launch_sddmm(dtype, t->nnz, k, t->rows, col_idx, X, k == 1 ? 1 : ldx, dY, k == 1 ? 1 : lddy, dvals, s);
     if (e != cudaSuccess) return cuda_fail(e, "SDDMM launch");
   }

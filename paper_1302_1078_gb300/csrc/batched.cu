@@ -124,7 +124,10 @@ __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __r
         if (threadIdx.x == 0) *d.done = 0;
       }
     }
-    __syncthreads();  // shared memory is reused by the next item; s_item has been read
+    // every thread read s_item before the item's first internal barrier, and no thread reads
+    // shared memory after the item's last barrier (ROWS: the last tile pass ends with one; MERGE:
+    // the barrier before the completion count), so the next item's index is published, and the
+    // shared memory handed over, with a single barrier
     if (threadIdx.x == 0) s_item = claimed;
     __syncthreads();
   }

@@ -70,15 +70,14 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
 
+  // the block's nonzero range straight from global memory (the same two words for every thread),
+  // so that the row pointers and the first tile are staged together, before one barrier
+  const int bs = __ldg(a.row_ptr + r0), be = __ldg(a.row_ptr + r0 + nrows);
   for (int i = threadIdx.x; i <= nrows; i += blockDim.x) s_rp[i] = ld_stream(a.row_ptr + r0 + i, pol_stream);
-  __syncthreads();
 
   const int g = threadIdx.x / LANES;
   const int lane = threadIdx.x % LANES;
   const bool active = g < nrows;
-  const int rs = active ? s_rp[g] : 0;
-  const int re = active ? s_rp[g + 1] : 0;
-  const int bs = s_rp[0], be = s_rp[nrows];
 
   // column slice of this lane (SpMM): [c_lo, c_lo + VEC) clipped to k
   const int c_lo = SPLIT ? 0 : lane * VEC;
@@ -95,16 +94,23 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
   };
 
   // passes over the block's nonzeros [bs, be), tile at a time (c0 + tile is never formed past be,
-  // so positions near 2^31 do not overflow)
-  for (int c0 = bs, c1 = 0; c0 < be; c0 = c1) {
-    c1 = be - c0 > tile ? c0 + tile : be;
+  // so positions near 2^31 do not overflow); each pass stages its tile, then one barrier, then
+  // computes, then one barrier before the next pass overwrites the tile
+  auto stage = [&](int c0, int c1) {
     const int a0 = c0 & ~3;
     if constexpr (PERM)
       stage_copy<int>(reinterpret_cast<int*>(s_val), a.perm, a0, c1, a.aligned_vals, pol_stream);
     else
       stage_copy<T>(s_val, a.vals, a0, c1, a.aligned_vals, pol_stream);
     stage_copy<int>(s_col, a.col_idx, a0, c1, a.aligned_cols, pol_stream);
-    __syncthreads();
+  };
+  int c1 = be - bs > tile ? bs + tile : be;
+  if (bs < be) stage(bs, c1);
+  __syncthreads();  // row pointers and the first tile
+  const int rs = active ? s_rp[g] : 0;
+  const int re = active ? s_rp[g + 1] : 0;
+  for (int c0 = bs; c0 < be;) {
+    const int a0 = c0 & ~3;
     if (active && col_active) {
       const int lo = max(rs, c0), hi = min(re, c1);
       constexpr int STEP = SPLIT ? LANES : 1;
@@ -151,7 +157,13 @@ __device__ __forceinline__ void rows_block(const RowsArgs<T>& a, int block) {
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // the tile has been read
+    c0 = c1;
+    if (c0 < be) {
+      c1 = be - c0 > tile ? c0 + tile : be;
+      stage(c0, c1);
+      __syncthreads();
+    }
   }
 
   if constexpr (SPLIT) {
