@@ -253,18 +253,20 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
     const bool active = g < nr;
     Acc<T> acc[VEC];
     DFAcc eacc[EMUL > 0 ? VEC : 1];
-    if (active && col_active) {
-      const int rs = rp[g], re = rp[g + 1];
-      constexpr int STEP = SPLIT ? LANES : 1;
-      int p = rs + (SPLIT ? lane : 0);
-      if constexpr (SPLIT) {
+    if constexpr (SPLIT) {
+      {
         // SpMV: software-pipelined walk of this lane's nonzeros p, p + STEP, ... < re.  The
         // gathers of group q + 1 are issued before the FMAs of group q wait for theirs, and
         // the last 0..3 nonzeros are gathered together, so a row costs about one round trip
         // to L2 per two groups instead of one per group and one per leftover nonzero.  The
         // products are added in the same order as a plain walk (with EMUL > 0 the first
         // EMUL products of every full group go to the float-float accumulator, flushed
-        // into the double one every 16 groups).
+        // into the double one every 16 groups).  Every lane of the warp runs the walk (a lane
+        // without a row has no nonzeros), so that the tail can skip warp-wide a product no
+        // lane needs: a warp FP64 instruction costs its full pipe slot whatever its mask.
+        const int rs = active ? rp[g] : 0, re = active ? rp[g + 1] : 0;
+        constexpr int STEP = LANES;
+        const int p = rs + lane;
         const int cnt = p < re ? (re - p + STEP - 1) / STEP : 0;
         const int full = cnt / kUnroll;
         T va[kUnroll], vb[kUnroll];
@@ -323,22 +325,37 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           }
         }
         const int rem = cnt - full * kUnroll;
-        if (rem > 0) {
-          const int q0 = full * kUnroll;
+        const int q0 = full * kUnroll;
 #pragma unroll
-          for (int u = 0; u < kUnroll - 1; ++u)
+        for (int u = 0; u < kUnroll - 1; ++u)
+          if (u < rem) {
+            vb[u] = sv[p + (q0 + u) * STEP - a0];
+            xb[u] = ld_keep(Xc + (long long)sc[p + (q0 + u) * STEP - a0] * a.ldx, pol_keep);
+          }
+        // A guarded product would be computed on every lane and kept by a select (a multiply-add
+        // has no side effects, so the compiler may lift it out of its branch).  For double values
+        // the product is a volatile instruction, which runs only on the lanes that need it, and a
+        // warp-wide test skips a product no lane needs.  (Counting the tail's products by a warp
+        // vote in a loop issues fewer FP64 instructions but was slower: the vote serialises.)
+#pragma unroll
+        for (int u = 0; u < kUnroll - 1; ++u)
+          if (__any_sync(0xffffffffu, u < rem)) {
             if (u < rem) {
-              vb[u] = sv[p + (q0 + u) * STEP - a0];
-              xb[u] = ld_keep(Xc + (long long)sc[p + (q0 + u) * STEP - a0] * a.ldx, pol_keep);
+              if constexpr (sizeof(T) == 8)
+                asm volatile("fma.rn.f64 %0, %1, %2, %0;" : "+d"(acc[0].s) : "d"(vb[u]), "d"(xb[u]));
+              else
+                acc[0].add(vb[u], xb[u]);
             }
-#pragma unroll
-          for (int u = 0; u < kUnroll - 1; ++u)
-            if (u < rem) acc[0].add(vb[u], xb[u]);
-        }
+          }
         // one lane per row: fold the float-float partial in now; several lanes: the row's
         // reduction merges the lanes' pairs in FP32 and converts once per row
         if constexpr (EMUL > 0 && LANES == 1) acc[0].add_partial((T)eacc[0].value());
-      } else if (EMUL == 0 && col_full) {
+      }
+    } else if (active && col_active) {
+      const int rs = rp[g], re = rp[g + 1];
+      constexpr int STEP = 1;
+      int p = rs;
+      if (EMUL == 0 && col_full) {
         // SpMM (the lane owns VEC columns and walks the whole row): the same software
         // pipeline as the SpMV walk, each gather a VEC-wide slice of an X row
         const int cnt = re - p;
