@@ -267,49 +267,73 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     };
     int nz = nz_s;
     if (a.aligned_vals && a.aligned_cols) {
-      for (; nz < nz_e && (nz & 3); ++nz) one(nz);
-      for (; nz + 4 <= nz_e; nz += 4) {
+      // aligned groups of four from the one holding nz_s to the one holding nz_e - 1, each read
+      // with vector loads; the entries of a group outside [nz_s, nz_e) belong to the neighbouring
+      // threads and are skipped (a scalar read of a segment's ragged ends would cost an L2
+      // request per 8-byte value and per 4-byte column id); only a group that runs past the end
+      // of the arrays is read element by element
+      for (int g = nz_s & ~3; g < nz_e; g += 4) {
         T v[4];
-        if constexpr (PERM) {
-          const uint4 pw = ld_stream_l1_v4(a.perm + nz, pol_stream);
-          v[0] = __ldg(a.vals + (int)pw.x);
-          v[1] = __ldg(a.vals + (int)pw.y);
-          v[2] = __ldg(a.vals + (int)pw.z);
-          v[3] = __ldg(a.vals + (int)pw.w);
-        } else if constexpr (sizeof(T) == 8) {
-          if (a.vals32) {
-            ld_stream_4d(reinterpret_cast<const double*>(a.vals + nz), pol_stream, reinterpret_cast<double*>(v));
+        int c4[4];
+        if (g + 4 <= a.nnz) {
+          if constexpr (PERM) {
+            const uint4 pw = ld_stream_l1_v4(a.perm + g, pol_stream);
+            const int pq[4] = {(int)pw.x, (int)pw.y, (int)pw.z, (int)pw.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (g + u >= nz_s && g + u < nz_e) v[u] = __ldg(a.vals + pq[u]);
+          } else if constexpr (sizeof(T) == 8) {
+            if (a.vals32) {
+              ld_stream_4d(reinterpret_cast<const double*>(a.vals + g), pol_stream, reinterpret_cast<double*>(v));
+            } else {
+              const uint4 w0 = ld_stream_l1_v4(a.vals + g, pol_stream);
+              const uint4 w1 = ld_stream_l1_v4(a.vals + g + 2, pol_stream);
+              v[0] = __hiloint2double((int)w0.y, (int)w0.x);
+              v[1] = __hiloint2double((int)w0.w, (int)w0.z);
+              v[2] = __hiloint2double((int)w1.y, (int)w1.x);
+              v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+            }
           } else {
-            const uint4 w0 = ld_stream_l1_v4(a.vals + nz, pol_stream);
-            const uint4 w1 = ld_stream_l1_v4(a.vals + nz + 2, pol_stream);
-            v[0] = __hiloint2double((int)w0.y, (int)w0.x);
-            v[1] = __hiloint2double((int)w0.w, (int)w0.z);
-            v[2] = __hiloint2double((int)w1.y, (int)w1.x);
-            v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+            const uint4 w = ld_stream_l1_v4(a.vals + g, pol_stream);
+            v[0] = __uint_as_float(w.x);
+            v[1] = __uint_as_float(w.y);
+            v[2] = __uint_as_float(w.z);
+            v[3] = __uint_as_float(w.w);
           }
+          const uint4 cw = ld_stream_l1_v4(a.col_idx + g, pol_stream);
+          c4[0] = (int)cw.x;
+          c4[1] = (int)cw.y;
+          c4[2] = (int)cw.z;
+          c4[3] = (int)cw.w;
         } else {
-          const uint4 w = ld_stream_l1_v4(a.vals + nz, pol_stream);
-          v[0] = __uint_as_float(w.x);
-          v[1] = __uint_as_float(w.y);
-          v[2] = __uint_as_float(w.z);
-          v[3] = __uint_as_float(w.w);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (g + u >= nz_s && g + u < nz_e) {
+              if constexpr (PERM)
+                v[u] = __ldg(a.vals + ld_stream(a.perm + g + u, pol_stream));
+              else
+                v[u] = ld_stream(a.vals + g + u, pol_stream);
+              c4[u] = ld_stream(a.col_idx + g + u, pol_stream);
+            }
         }
-        const uint4 cw = ld_stream_l1_v4(a.col_idx + nz, pol_stream);
-        const int c4[4] = {(int)cw.x, (int)cw.y, (int)cw.z, (int)cw.w};
         Vec<T, VEC> xv[4];
         if (col_active) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) xv[u] = gather(c4[u]);
+          for (int u = 0; u < 4; ++u)
+            if (g + u >= nz_s && g + u < nz_e) xv[u] = gather(c4[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          close_rows(nz + u);
-          if (col_active) {
+          if (g + u >= nz_s && g + u < nz_e) {
+            close_rows(g + u);
+            if (col_active) {
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+              for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+            }
           }
         }
       }
+      nz = nz_e;
     }
     for (; nz < nz_e; ++nz) one(nz);
   } else {
@@ -444,16 +468,38 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of
 // equal carry rows sums the run in CTA order and adds it to Y (row finished by a
-// later CTA, which has already written its own part).
+// later CTA, which has already written its own part).  A hub row spans tens of
+// tiles, so the run's end and its carries are read 8 tiles at a time with
+// independent loads; the additions stay in CTA order.
 template <typename T>
 __device__ __forceinline__ void merge_fixup_one(int b, int ctas, int k, const int* __restrict__ carry_row,
                                                 const T* __restrict__ carry_val, T* __restrict__ Y, long long ldy) {
+  constexpr int W = 8;
   const int r = __ldcg(carry_row + b);
   if (r < 0) return;
   if (b > 0 && __ldcg(carry_row + b - 1) == r) return;
+  int e = b + 1;  // the run is [b, e)
+  for (;;) {
+    int rr[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) rr[j] = e + j < ctas ? __ldcg(carry_row + e + j) : -2;
+    int stop = W;
+#pragma unroll
+    for (int j = W - 1; j >= 0; --j)
+      if (rr[j] != r) stop = j;
+    e += stop;
+    if (stop < W) break;
+  }
   for (int c = 0; c < k; ++c) {
     Acc<T> s;
-    for (int bb = b; bb < ctas && __ldcg(carry_row + bb) == r; ++bb) s.add_partial(__ldcg(carry_val + (size_t)bb * k + c));
+    for (int bb = b; bb < e; bb += W) {
+      T v[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) v[j] = bb + j < e ? __ldcg(carry_val + (size_t)(bb + j) * k + c) : T(0);
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (bb + j < e) s.add_partial(v[j]);
+    }
     T* yp = Y + (long long)r * ldy + c;
     *yp = __ldcg(yp) + s.value();
   }
