@@ -75,9 +75,17 @@ typedef enum {
   GBS_VARIANT_ROWS_TMA = 3, /* ROWS with persistent CTAs and a double-buffered bulk-copy (TMA)
                               pipeline; plans only (the plan sizes the tile to the largest
                               row block); needs 16-byte aligned vals and col_idx, else runs as ROWS */
-  GBS_VARIANT_MERGE_DIRECT = 4 /* merge-path whose threads load their own nonzeros from global
+  GBS_VARIANT_MERGE_DIRECT = 4, /* merge-path whose threads load their own nonzeros from global
                                   memory in 128-bit groups (no shared-memory staging of vals /
                                   col_idx), so more items per thread fit */
+  GBS_VARIANT_ROWS_DIRECT = 5 /* ROWS without shared memory or barriers: every lane reads its
+                                 row's values and column ids itself through L1 and walks the
+                                 whole row; k > 1: `lanes` lanes split the columns, as in ROWS;
+                                 k == 1: one lane per row (lanes ignored).  Same results, bit
+                                 for bit, as ROWS with lanes that split the columns (k > 1) or
+                                 with one lane per row (k == 1); for short rows and batched
+                                 items.  Values are not read through a permutation (not for the
+                                 backward pass's A^T) */
 } gbs_variant;
 
 /*

@@ -94,6 +94,7 @@ int default_items(int g, int threads) {
 gbs_config normalize(const gbs_config& c, int dtype) {
   gbs_config r = c;
   if (r.threads <= 0) r.threads = 256;
+  if (r.variant == GBS_VARIANT_ROWS_DIRECT && r.lanes <= 0) r.lanes = 1;
   if (r.variant == GBS_VARIANT_ROWS || r.variant == GBS_VARIANT_ROWS_TMA) {
     if (r.lanes <= 0) r.lanes = 1;
     if (r.tile_nnz <= 0) r.tile_nnz = dtype == GBS_F64 ? 2048 : 3072;
@@ -107,8 +108,9 @@ struct MergeGeom {
 };
 
 int check_cfg(const gbs_config& c) {
-  if (c.variant != GBS_VARIANT_ROWS && !is_merge(c.variant) && c.variant != GBS_VARIANT_ROWS_TMA)
-    return fail(GBS_EINVAL, "variant must be ROWS, MERGE, ROWS_TMA or MERGE_DIRECT after resolution");
+  if (c.variant != GBS_VARIANT_ROWS && !is_merge(c.variant) && c.variant != GBS_VARIANT_ROWS_TMA &&
+      c.variant != GBS_VARIANT_ROWS_DIRECT)
+    return fail(GBS_EINVAL, "variant must be ROWS, MERGE, ROWS_TMA, MERGE_DIRECT or ROWS_DIRECT after resolution");
   if (c.variant == GBS_VARIANT_ROWS_TMA && c.threads > 256) return fail(GBS_EINVAL, "ROWS_TMA threads must be <= 256");
   if (c.threads % 32 != 0 || c.threads < 32 || c.threads > 1024) return fail(GBS_EINVAL, "threads must be 32..1024, multiple of 32");
   if (is_merge(c.variant) && c.threads > 256) return fail(GBS_EINVAL, "MERGE threads must be <= 256");
@@ -190,6 +192,19 @@ int run_product(const CsrView& A, int dtype, int k, const void* X, long long ldx
       e = dtype == GBS_F64 ? launch_rows_tma_f64(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, cfg.emul, status, s)
                            : launch_rows_tma_f32(A, D, lanes, vec16, cfg.threads, cfg.tile_nnz, 0, status, s);
       if (e != cudaSuccess) return cuda_fail(e, "ROWS_TMA launch");
+    }
+    return GBS_OK;
+  }
+  if (cfg.variant == GBS_VARIANT_ROWS_DIRECT) {
+    if (perm) return fail(GBS_EUNSUPPORTED, "ROWS_DIRECT does not read values through a permutation");
+    for (int c0 = 0; c0 < k; c0 += P) {
+      const int kp = std::min(P, k - c0);
+      int lanes = cfg.lanes;
+      if (k > 1) lanes = std::max(lanes, col_lanes(kp, dtype, vec16));
+      DenseView D{kp, static_cast<const char*>(X) + c0 * es, ldx, static_cast<char*>(Y) + c0 * es, ldy};
+      e = dtype == GBS_F64 ? launch_rows_direct_f64(A, D, lanes, vec16, cfg.threads, s)
+                           : launch_rows_direct_f32(A, D, lanes, vec16, cfg.threads, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ROWS_DIRECT launch");
     }
     return GBS_OK;
   }
@@ -823,6 +838,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     for (int it : {7, 11, 15, 23, 31}) add(GBS_VARIANT_MERGE, 0, 256, 0, it);
     for (int it : {7, 11, 15, 23, 31, 47, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, it);
     for (int it : {31, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 128, 0, it);
+    for (int th : {128, 256}) add(GBS_VARIANT_ROWS_DIRECT, 1, th, 0, 0);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, 128, base_tile, 0);
@@ -839,6 +855,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     add(GBS_VARIANT_MERGE, 0, 256, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 128, 0, 0);
     add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, 0);
+    for (int th : {128, 256}) add(GBS_VARIANT_ROWS_DIRECT, 0, th, 0, 0);
   }
   // skewed column degrees (a power-law matrix): the merge forms again on columns relabelled
   // hottest first, with every gather through L1 or with the cold ones bypassing it
@@ -861,7 +878,7 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     // values through a permutation: the variants that support it
     std::vector<gbs_config> keep;
     for (const gbs_config& g : c)
-      if (g.variant != GBS_VARIANT_ROWS_TMA && g.emul == 0) keep.push_back(g);
+      if (g.variant != GBS_VARIANT_ROWS_TMA && g.variant != GBS_VARIANT_ROWS_DIRECT && g.emul == 0) keep.push_back(g);
     c.swap(keep);
   }
   return c;
@@ -1301,6 +1318,8 @@ int gbs_tplan_set_config(gbs_tplan* t, int dtype, int k, const gbs_config* cfg, 
   if (!t || !cfg) return fail(GBS_EINVAL, "NULL pointer");
   if (!valid_dtype(dtype)) return fail(GBS_EDTYPE, "dtype");
   if (k < 1) return fail(GBS_EINVAL, "k must be >= 1");
+  if (cfg->variant == GBS_VARIANT_ROWS_DIRECT)
+    return fail(GBS_EUNSUPPORTED, "ROWS_DIRECT does not read values through the transpose permutation");
   const bool gather = cfg->variant == GBS_VARIANT_ROWS_TMA;
   gbs_plan* p = nullptr;
   int rc = plan_create_impl(&p, t->n, t->m, t->nnz, t->rptrT, t->colT, dtype, k, 0, gather ? nullptr : t->perm,
@@ -1593,12 +1612,14 @@ std::vector<gbs_config> batch_candidates(const gbs_stats& st, int dtype, int k) 
     for (int l : {1, 2, 4, 8, 16, 32})
       if (l == 1 || st.mean_row >= 0.5 * l) add(GBS_VARIANT_ROWS, l, base_tile, 0);
     for (int it : {7, 15, 31}) add(GBS_VARIANT_MERGE, 0, 0, it);
+    add(GBS_VARIANT_ROWS_DIRECT, 1, 0, 0);
   } else {
     add(GBS_VARIANT_ROWS, 0, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile / 2, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile * 2, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 15);
+    add(GBS_VARIANT_ROWS_DIRECT, 0, 0, 0);
   }
   return c;
 }
@@ -1638,15 +1659,17 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
   struct Policy {
     bool from_stats;  // statistics' variant (else the per-matrix choice)
     int rows_tile;    // ROWS tile when from_stats
-    double short_row; // mean row below which a matrix takes MERGE (0: none)
+    double short_row; // mean row below which a matrix takes `short_variant` (0: none)
     int merge_items;  // items per merge thread for the MERGE matrices (0: default)
+    int short_variant;  // MERGE, or ROWS_DIRECT (no staging, no barriers)
   };
   std::vector<Policy> policies;
-  // (merge tiles larger than the default were slower in every policy on the 512-matrix k = 8
-  // batch, so the items dimension stays at the default)
+  // (on the 512-matrix k = 8 batch every policy was slower with merge tiles larger or smaller
+  // than the default, and with ROWS_DIRECT matrices, whether for the short rows or for all the
+  // statistics' ROWS matrices, so neither is tried)
   for (double thr : {0.0, 8.0, 12.0, 20.0}) {
-    policies.push_back({false, 0, thr, 0});
-    for (int t : {base_tile, 2 * base_tile}) policies.push_back({true, t, thr, 0});
+    policies.push_back({false, 0, thr, 0, GBS_VARIANT_MERGE});
+    for (int t : {base_tile, 2 * base_tile}) policies.push_back({true, t, thr, 0, GBS_VARIANT_MERGE});
   }
   int pol_id = 0;
   for (const Policy& pol : policies) {
@@ -1662,7 +1685,7 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
       }
       if (pol.short_row > 0.0 && st.mean_row < pol.short_row) {
         c = gbs_config{};
-        c.variant = GBS_VARIANT_MERGE;
+        c.variant = pol.short_variant;
       }
       if (c.variant == GBS_VARIANT_MERGE && (pol.from_stats || pol.short_row > 0.0 || pol.merge_items > 0))
         c.items = pol.merge_items;
@@ -1677,8 +1700,9 @@ int spmv_csr_batched_plan(gbs_batch_plan** out, int nmat, const gbs_batch_item* 
     }
     const float ms = time_plan(q);
     if (tune_log())
-      std::fprintf(stderr, "gbspmv batch policy %d (stats %d tile %d short<%.0f items %d): %.4f ms (best %.4f ms)\n",
-                   pol_id, (int)pol.from_stats, pol.rows_tile, pol.short_row, pol.merge_items, ms, best_ms);
+      std::fprintf(stderr, "gbspmv batch policy %d (stats %d tile %d short<%.0f -> variant %d, items %d): %.4f ms "
+                   "(best %.4f ms)\n", pol_id, (int)pol.from_stats, pol.rows_tile, pol.short_row, pol.short_variant,
+                   pol.merge_items, ms, best_ms);
     if (ms > 0 && ms < best_ms) {
       batch_free(best);
       best = q;
@@ -1740,14 +1764,16 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
       gbs_config& g = given_cfgs[b];
       if (g.variant == GBS_VARIANT_AUTO) continue;
       int rc = GBS_OK;
-      if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE) {
-        rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": batched configurations are ROWS or MERGE");
+      if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE && g.variant != GBS_VARIANT_ROWS_DIRECT) {
+        rc = fail(GBS_EUNSUPPORTED,
+                  "item " + std::to_string(b) + ": batched configurations are ROWS, MERGE or ROWS_DIRECT");
       } else if (g.relabel != 0) {
         rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": column relabelling is for plans of one matrix");
       } else {
         g.threads = kBatchThreads;
         g.emul = 0;
-        if (g.variant == GBS_VARIANT_ROWS && k > 1) g.lanes = p->G;
+        if ((g.variant == GBS_VARIANT_ROWS || g.variant == GBS_VARIANT_ROWS_DIRECT) && k > 1) g.lanes = p->G;
+        if (g.variant == GBS_VARIANT_ROWS_DIRECT && k == 1) g.lanes = 1;
         g = normalize(g, dtype);
         rc = check_cfg(g);
       }
@@ -1781,7 +1807,7 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
     if (tune && !given && it.m > 0) {
       float best = 1e30f;
       for (gbs_config cand : batch_candidates(st, dtype, k)) {
-        if (k > 1 && cand.variant == GBS_VARIANT_ROWS) cand.lanes = p->G;
+        if (k > 1 && (cand.variant == GBS_VARIANT_ROWS || cand.variant == GBS_VARIANT_ROWS_DIRECT)) cand.lanes = p->G;
         if (is_merge(cand.variant)) {
           // time the tile size the batch will run (capped to the shared-memory budget)
           const MergeGeom G = merge_geom(cand, it.m, it.nnz, dtype, k, vec16);
@@ -1821,7 +1847,13 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
     const gbs_batch_item& it = p->items[b];
     const gbs_config& c = p->cfgs[b];
     long long nitems = 0;
-    if (c.variant == GBS_VARIANT_ROWS) {
+    if (c.variant == GBS_VARIANT_ROWS_DIRECT) {
+      // no shared memory: one item per block of rows
+      const int lanes = k == 1 ? 1 : p->G;
+      p->cfgs[b].lanes = lanes;
+      const int rpc = kBatchThreads / lanes;
+      nitems = (it.m + rpc - 1) / rpc;
+    } else if (c.variant == GBS_VARIANT_ROWS) {
       const int lanes = k == 1 ? c.lanes : p->G;
       const int rpc = kBatchThreads / lanes;
       nitems = (it.m + rpc - 1) / rpc;
@@ -1950,7 +1982,7 @@ int spmv_csr_batched_looped(gbs_batch_plan* p, void* stream) {
     if (it.m == 0) continue;
     CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
     gbs_config c = p->cfgs[b];
-    if (c.variant == GBS_VARIANT_ROWS && p->k > 1) c.lanes = p->G;
+    if ((c.variant == GBS_VARIANT_ROWS || c.variant == GBS_VARIANT_ROWS_DIRECT) && p->k > 1) c.lanes = p->G;
     MergeBuffers mb = p->mbs[b];
     int rc = run_product(A, p->dtype, p->k, it.X, p->k == 1 ? 1 : it.ldx, it.Y, p->k == 1 ? 1 : it.ldy, c,
                          is_merge(c.variant) ? &mb : nullptr, true, s);

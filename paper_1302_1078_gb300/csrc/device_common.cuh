@@ -79,6 +79,12 @@ __device__ __forceinline__ float ld_keep(const float* ptr, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(ptr), "l"(pol));
   return r;
 }
+__device__ __forceinline__ int ld_keep(const int* ptr, uint64_t pol) {
+  int r;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(ptr), "l"(pol));
+  return r;
+}
+
 // The same gathers without L1 allocation: for the entries of x that are rarely reused (the cold
 // columns of a relabelled matrix), so that they do not evict the hot ones from L1.
 __device__ __forceinline__ double ld_keep_na(const double* ptr, uint64_t pol) {

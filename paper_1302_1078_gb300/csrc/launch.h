@@ -39,6 +39,13 @@ cudaError_t launch_rows_f64(const CsrView& A, const DenseView& D, int lanes, boo
 cudaError_t launch_rows_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads, int tile,
                             int row_base, int rows, cudaStream_t s);
 
+// ROWS_DIRECT variant (no shared memory, no barriers): lanes split the columns (k > 1; same
+// rules as ROWS), one lane per row for k == 1; values are not read through a permutation.
+cudaError_t launch_rows_direct_f64(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads,
+                                   cudaStream_t s);
+cudaError_t launch_rows_direct_f32(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads,
+                                   cudaStream_t s);
+
 // ROWS_TMA variant (persistent, bulk-copy pipeline).  tile must hold the largest block's
 // nonzeros + 8; vals and col_idx 16-byte aligned; status: device int (bit 0 = wait timeout).
 // emul (FP64 only, 0..3): products per group of 4 nonzeros computed on the FP32 pipe (df64.cuh).

@@ -69,6 +69,52 @@ cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool 
   }
 }
 
+template <typename T, int VEC, int LANES>
+static cudaError_t rows_direct_go(const RowsArgs<T>& a, int grid, int threads, cudaStream_t s) {
+  rows_direct_kernel<T, VEC, LANES><<<grid, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int LANES>
+static cudaError_t rows_direct_lanes(const RowsArgs<T>& a, bool vec16, int grid, int threads, cudaStream_t s) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if (vec16) return rows_direct_go<T, V, LANES>(a, grid, threads, s);
+  return rows_direct_go<T, 1, LANES>(a, grid, threads, s);
+}
+
+// ROWS_DIRECT (rows_direct_block): k == 1 runs one lane per row whatever `lanes` says.
+template <typename T>
+cudaError_t launch_rows_direct_t(const CsrView& A, const DenseView& D, int lanes, bool vec16, int threads,
+                                 cudaStream_t s) {
+  if (A.m <= 0) return cudaSuccess;
+  RowsArgs<T> a;
+  a.m = A.m;
+  a.k = D.k;
+  a.row_ptr = A.row_ptr;
+  a.col_idx = A.col_idx;
+  a.vals = static_cast<const T*>(A.vals);
+  a.X = static_cast<const T*>(D.X);
+  a.Y = static_cast<T*>(D.Y);
+  a.ldx = D.ldx;
+  a.ldy = D.ldy;
+  a.tile = 0;
+  a.row_base = 0;
+  a.aligned_vals = false;
+  a.aligned_cols = false;
+  if (D.k == 1) lanes = 1;
+  const int rpc = threads / lanes;
+  const int grid = (A.m + rpc - 1) / rpc;
+  switch (lanes) {
+    case 1: return rows_direct_lanes<T, 1>(a, vec16 && D.k > 1, grid, threads, s);
+    case 2: return rows_direct_lanes<T, 2>(a, vec16, grid, threads, s);
+    case 4: return rows_direct_lanes<T, 4>(a, vec16, grid, threads, s);
+    case 8: return rows_direct_lanes<T, 8>(a, vec16, grid, threads, s);
+    case 16: return rows_direct_lanes<T, 16>(a, vec16, grid, threads, s);
+    case 32: return rows_direct_lanes<T, 32>(a, vec16, grid, threads, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T, int VEC, int LANES, bool SPLIT, int EMUL>
 static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* status, int threads, size_t smem,
                                cudaStream_t s) {

@@ -192,4 +192,81 @@ __global__ void __launch_bounds__(1024) rows_kernel(RowsArgs<T> a) {
   rows_block<T, VEC, LANES, SPLIT, PERM>(a, blockIdx.x);
 }
 
+// ROWS_DIRECT: the row-wise arithmetic of rows_block without shared memory.  Every lane loads
+// its row's values and column ids itself, through L1 (the lanes of a row read the same words, so
+// one request serves them all, and the next words of the row then hit L1), and walks the whole
+// row, so a block has no barrier at all.  This is for short rows, where staging a tile and its
+// barriers cost more than the products (a 64-row block of a 5-point stencil holds 320
+// nonzeros), and for the batched kernel, where every block is a work item.  k > 1: LANES lanes
+// split the columns, VEC each; k == 1: one lane per row (LANES == 1).  Each lane sums its
+// products in stored order, as rows_block does with lanes that split the columns (or with one
+// lane per row), so the two variants give the same bits.
+template <typename T, int VEC, int LANES, bool PERM = false>
+__device__ __forceinline__ void rows_direct_block(const RowsArgs<T>& a, int block) {
+  const int rpc = blockDim.x / LANES;
+  const int r = a.row_base + block * rpc + (int)threadIdx.x / LANES;
+  const int c_lo = ((int)threadIdx.x % LANES) * VEC;
+  if (r >= a.m || c_lo >= a.k) return;
+  const bool col_full = c_lo + VEC <= a.k;
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  const int rs = ld_keep(a.row_ptr + r, pol_stream), re = ld_keep(a.row_ptr + r + 1, pol_stream);
+  auto val_at = [&](int p) -> T {
+    if constexpr (PERM)
+      return __ldg(a.vals + ld_keep(a.perm + p, pol_stream));
+    else
+      return ld_keep(a.vals + p, pol_stream);
+  };
+  const T* __restrict__ Xc = a.X + c_lo;
+  Acc<T> acc[VEC];
+  int p = rs;
+  if (col_full) {
+    for (; p + kUnroll <= re; p += kUnroll) {
+      T v[kUnroll];
+      int c[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        v[u] = val_at(p + u);
+        c[u] = ld_keep(a.col_idx + p + u, pol_stream);
+      }
+      Vec<T, VEC> xv[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) acc[j].add(v[u], xv[u].v[j]);
+    }
+    for (; p < re; ++p) {
+      const T v = val_at(p);
+      Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)ld_keep(a.col_idx + p, pol_stream) * a.ldx, pol_keep);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) acc[j].add(v, xv.v[j]);
+    }
+  } else {
+    // ragged last column slice: scalar gathers of the valid columns
+    const int nv = a.k - c_lo;
+    for (; p < re; ++p) {
+      const T v = val_at(p);
+      const T* xr = Xc + (long long)ld_keep(a.col_idx + p, pol_stream) * a.ldx;
+#pragma unroll
+      for (int j = 0; j < VEC; ++j)
+        if (j < nv) acc[j].add(v, ld_keep(xr + j, pol_keep));
+    }
+  }
+  T out[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
+  T* yr = a.Y + (long long)r * a.ldy + c_lo;
+  if (col_full)
+    st_stream_vec<T, VEC>(yr, out);
+  else
+    for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+}
+
+template <typename T, int VEC, int LANES, bool PERM = false>
+__global__ void __launch_bounds__(1024) rows_direct_kernel(RowsArgs<T> a) {
+  rows_direct_block<T, VEC, LANES, PERM>(a, blockIdx.x);
+}
+
 }  // namespace gbs

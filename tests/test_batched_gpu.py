@@ -59,7 +59,7 @@ def test_batched_equals_looped_and_oracle(gbs, k, dtype, tune):
     ib = info["item_begin"]
     assert ib[0] == 0 and all(b >= a for a, b in zip(ib, ib[1:])) and ib[-1] == info["total_items"]
     variants = {c["variant"] for c in info["configs"]}
-    assert variants <= {1, 2}
+    assert variants <= {1, 2, 5}
     plan.run()
     torch.cuda.synchronize()
     batched = [y.clone() for y in Ys]
@@ -99,11 +99,11 @@ def test_batched_forced_merge_and_new_operands(gbs):
 @pytest.mark.parametrize("k,dtype", [(8, torch.float64), (1, torch.float64), (1, torch.float32)],
                          ids=["k8f64", "k1f64", "k1f32"])
 def test_batched_explicit_configs(gbs, k, dtype):
-    """Caller-given per-matrix configurations (ROWS / MERGE / library's choice): equal to the
-    per-matrix loop bitwise and to the oracle; other variants are refused."""
+    """Caller-given per-matrix configurations (ROWS / MERGE / ROWS_DIRECT / library's choice):
+    equal to the per-matrix loop bitwise and to the oracle; other variants are refused."""
     mats, Xs, Ys, host = make_batch(SMALL[:18], k, dtype, seed=9)
     cycle = [dict(variant=2, items=5), dict(variant=1, lanes=2, tile_nnz=96), None,
-             dict(variant=2, items=63), dict(variant=1, lanes=1, tile_nnz=4096), dict(variant=0)]
+             dict(variant=2, items=63), dict(variant=1, lanes=1, tile_nnz=4096), dict(variant=0), dict(variant=5)]
     cfgs = [cycle[b % len(cycle)] for b in range(len(mats))]
     plan = gbs.BatchedPlan(mats, Xs, Ys, configs=cfgs)
     info = plan.info()

@@ -96,7 +96,8 @@ CONFIGS = [None,
            dict(variant=2, items=1), dict(variant=2, items=4), dict(variant=2, items=16, threads=64),
            dict(variant=2, items=7, threads=96),
            dict(variant=4, items=1), dict(variant=4, items=5), dict(variant=4, items=31),
-           dict(variant=4, items=63, threads=128), dict(variant=4, items=9, threads=96)]
+           dict(variant=4, items=63, threads=128), dict(variant=4, items=9, threads=96),
+           dict(variant=5), dict(variant=5, threads=64), dict(variant=5, threads=1024)]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
@@ -129,7 +130,8 @@ def test_spmm_parity(gbs, name, k, dtype):
     Xd_wide = torch.from_numpy(Xw).cuda()
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     for cfg in [None, dict(variant=1), dict(variant=1, threads=128, tile_nnz=500), dict(variant=2),
-                dict(variant=2, items=3, threads=128), dict(variant=4), dict(variant=4, items=13, threads=128)]:
+                dict(variant=2, items=3, threads=128), dict(variant=4), dict(variant=4, items=13, threads=128),
+                dict(variant=5), dict(variant=5, threads=96)]:
         for XX in (Xd, Xd_wide[:, :k]):
             Y = torch.full((A.m, k), float("nan"), dtype=dtype, device="cuda")
             gbs.spmm_csr(rp, ci, v, XX, Y, config=cfg)
@@ -225,6 +227,31 @@ def test_untuned_plan_picks_the_kernel_from_row_lengths(gbs, dtype):
             assert cfg["lanes"] == 1 or mean > per * (cfg["lanes"] // 2), (name, cfg)
         assert_close(plan.spmv(v, xd), y_ref, r, dtype, f"untuned plan {name} {cfg}")
         assert_close(gbs.spmv_csr(rp, ci, v, xd), y_ref, r, dtype, f"one-shot {name}")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("k", [1, 3, 8, 16, 40])
+@pytest.mark.parametrize("name", ["stencil2d_37", "banded_30k", "rmat_14", "random_dup_unsorted", "hub", "empty_nnz"])
+def test_rows_direct_is_bitwise_rows(gbs, name, k, dtype):
+    """ROWS_DIRECT reads each row straight from global memory instead of a staged tile, with the
+    same per-lane order of products as ROWS whose lanes split the columns (k > 1) or with one lane
+    per row (k == 1): the two give the same bits, for aligned and narrow X, in every column panel."""
+    A = matrix(name)
+    rp, ci, v = dev_csr(A, dtype)
+    for ld in (k, k + 1):
+        Xw = synth.uniform(A.n * ld, seed=41, stream=ld).reshape(A.n, ld).astype(NP[dtype])
+        X = torch.from_numpy(Xw).cuda()[:, :k]
+        if k == 1:
+            xd = torch.from_numpy(np.ascontiguousarray(Xw[:, 0])).cuda()
+            y0 = gbs.spmv_csr(rp, ci, v, xd, config=dict(variant=1, lanes=1, tile_nnz=512))
+            for th in (64, 256):
+                y1 = gbs.spmv_csr(rp, ci, v, xd, config=dict(variant=5, threads=th))
+                assert torch.equal(y0, y1), (name, th)
+        else:
+            Y0 = gbs.spmm_csr(rp, ci, v, X, config=dict(variant=1, tile_nnz=512))
+            for th in (64, 256):
+                Y1 = gbs.spmm_csr(rp, ci, v, X, config=dict(variant=5, threads=th))
+                assert torch.equal(Y0, Y1), (name, k, ld, th)
 
 
 def test_stats_and_validation(gbs):
