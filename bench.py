@@ -107,16 +107,23 @@ def kernel_source_hash(variant: int) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(variant: int, matrix: str):
-    """DRAM bytes per launch from profiles/traffic.txt (lines: variant hash bytes matrix command...),
-    or None when no capture matches the current kernel source."""
+def traffic_key(variant: int, relabel: int = 0) -> str:
+    """Key of a configuration in profiles/traffic.txt: the variant, with rN appended for a plan that
+    relabels its columns (gbs_config.relabel N)."""
+    return f"{variant}r{relabel}" if relabel else str(variant)
+
+
+def recorded_traffic(variant: int, matrix: str, relabel: int = 0):
+    """DRAM bytes per launch from profiles/traffic.txt (lines: key hash bytes matrix command...),
+    or None when no capture matches the configuration and the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     want = kernel_source_hash(variant)
+    key = traffic_key(variant, relabel)
     for line in open(path):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == str(variant) and f[1] == want and f[3] == matrix:
+        if len(f) >= 4 and not line.startswith("#") and f[0] == key and f[1] == want and f[3] == matrix:
             return float(f[2])
     return None
 
@@ -599,7 +606,8 @@ def run_gpu(args, rank, world, local_rank):
     t_hbm = items[dom]["bytes"] / (hbm_peak * 1e9)
     t_alu = items[dom]["flops"] / (fp64_peak_gflops * 1e9)
     hbm_roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": d["hbm_frac"],
-                "traffic": recorded_traffic(d["config"]["variant"], d["matrix"]) if d["k"] == 1 else None,
+                "traffic": recorded_traffic(d["config"]["variant"], d["matrix"], d["config"].get("relabel", 0))
+                if d["k"] == 1 else None,
                 "algorithmic_bytes": items[dom]["bytes"], "kernel": f"{d['matrix']} k={d['k']} {d['config']}",
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"}
     alu_roof = {"bound": "alu", "achieved": d["gflops"], "peak": fp64_peak_gflops, "unit": "GFLOP/s",
@@ -746,7 +754,9 @@ def measure_batched(gbs, torch, dev, args, rank, world, steps, warmup, shard=Fal
     sampler = ClockSampler(gpu_smi_id(torch, dev.index or 0))
     sampler.start()
     time.sleep(0.05)
+    torch.cuda.nvtx.range_push("timed_batched")
     t_batched = timed(plan.run, steps)
+    torch.cuda.nvtx.range_pop()
     t_looped = timed(plan.run_looped, steps)
     t_looped_pm = timed(plan_pm.run_looped, steps)
     sampler.stop()

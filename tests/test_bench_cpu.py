@@ -55,15 +55,17 @@ def test_compulsory_bytes_closed_forms():
 
 
 def test_recorded_traffic_is_plausible():
-    """Every recorded DRAM figure names a kernel variant, a 16-hex-digit source hash and a benchmark
-    matrix, and lies within 10 % of that matrix's compulsory bytes (more would mean re-reads)."""
+    """Every recorded DRAM figure names a kernel variant (with rN for a relabelling plan), a
+    16-hex-digit source hash and a benchmark matrix, and lies within 10 % of that matrix's
+    compulsory bytes (more would mean re-reads)."""
     sizes = {"stencil3d_100": (10**6, 10**6, 26_463_592), "banded_2M_hbw1000_50": (2 * 10**6, 2 * 10**6, 10**8)}
     seen = 0
     for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
         if line.startswith("#") or not line.strip():
             continue
         f = line.split()
-        assert f[0] in ("1", "2", "3", "4")
+        assert f[0].split("r")[0] in ("1", "2", "3", "4", "5")
+        assert f[0] == bench.traffic_key(int(f[0].split("r")[0]), int(f[0].split("r")[1]) if "r" in f[0] else 0)
         assert len(f[1]) == 16 and int(f[1], 16) >= 0
         if f[3] in sizes:
             cb = bench.compulsory_bytes(*sizes[f[3]], 1)
