@@ -272,50 +272,38 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       // threads and are skipped (a scalar read of a segment's ragged ends would cost an L2
       // request per 8-byte value and per 4-byte column id); only a group that runs past the end
       // of the arrays is read element by element
-      for (int g = nz_s & ~3; g < nz_e; g += 4) {
+      // groups below vec_end lie wholly inside the arrays; the arrays' last partial group (only
+      // the matrix's last merge thread reaches it) is read element by element after the loop
+      const int vec_end = a.nnz & ~3;
+      int g = nz_s & ~3;
+      for (; g < nz_e && g < vec_end; g += 4) {
         T v[4];
-        int c4[4];
-        if (g + 4 <= a.nnz) {
-          if constexpr (PERM) {
-            const uint4 pw = ld_stream_l1_v4(a.perm + g, pol_stream);
-            const int pq[4] = {(int)pw.x, (int)pw.y, (int)pw.z, (int)pw.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (g + u >= nz_s && g + u < nz_e) v[u] = __ldg(a.vals + pq[u]);
-          } else if constexpr (sizeof(T) == 8) {
-            if (a.vals32) {
-              ld_stream_4d(reinterpret_cast<const double*>(a.vals + g), pol_stream, reinterpret_cast<double*>(v));
-            } else {
-              const uint4 w0 = ld_stream_l1_v4(a.vals + g, pol_stream);
-              const uint4 w1 = ld_stream_l1_v4(a.vals + g + 2, pol_stream);
-              v[0] = __hiloint2double((int)w0.y, (int)w0.x);
-              v[1] = __hiloint2double((int)w0.w, (int)w0.z);
-              v[2] = __hiloint2double((int)w1.y, (int)w1.x);
-              v[3] = __hiloint2double((int)w1.w, (int)w1.z);
-            }
-          } else {
-            const uint4 w = ld_stream_l1_v4(a.vals + g, pol_stream);
-            v[0] = __uint_as_float(w.x);
-            v[1] = __uint_as_float(w.y);
-            v[2] = __uint_as_float(w.z);
-            v[3] = __uint_as_float(w.w);
-          }
-          const uint4 cw = ld_stream_l1_v4(a.col_idx + g, pol_stream);
-          c4[0] = (int)cw.x;
-          c4[1] = (int)cw.y;
-          c4[2] = (int)cw.z;
-          c4[3] = (int)cw.w;
-        } else {
+        if constexpr (PERM) {
+          const uint4 pw = ld_stream_l1_v4(a.perm + g, pol_stream);
+          const int pq[4] = {(int)pw.x, (int)pw.y, (int)pw.z, (int)pw.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (g + u >= nz_s && g + u < nz_e) {
-              if constexpr (PERM)
-                v[u] = __ldg(a.vals + ld_stream(a.perm + g + u, pol_stream));
-              else
-                v[u] = ld_stream(a.vals + g + u, pol_stream);
-              c4[u] = ld_stream(a.col_idx + g + u, pol_stream);
-            }
+            if (g + u >= nz_s && g + u < nz_e) v[u] = __ldg(a.vals + pq[u]);
+        } else if constexpr (sizeof(T) == 8) {
+          if (a.vals32) {
+            ld_stream_4d(reinterpret_cast<const double*>(a.vals + g), pol_stream, reinterpret_cast<double*>(v));
+          } else {
+            const uint4 w0 = ld_stream_l1_v4(a.vals + g, pol_stream);
+            const uint4 w1 = ld_stream_l1_v4(a.vals + g + 2, pol_stream);
+            v[0] = __hiloint2double((int)w0.y, (int)w0.x);
+            v[1] = __hiloint2double((int)w0.w, (int)w0.z);
+            v[2] = __hiloint2double((int)w1.y, (int)w1.x);
+            v[3] = __hiloint2double((int)w1.w, (int)w1.z);
+          }
+        } else {
+          const uint4 w = ld_stream_l1_v4(a.vals + g, pol_stream);
+          v[0] = __uint_as_float(w.x);
+          v[1] = __uint_as_float(w.y);
+          v[2] = __uint_as_float(w.z);
+          v[3] = __uint_as_float(w.w);
         }
+        const uint4 cw = ld_stream_l1_v4(a.col_idx + g, pol_stream);
+        const int c4[4] = {(int)cw.x, (int)cw.y, (int)cw.z, (int)cw.w};
         Vec<T, VEC> xv[4];
         if (col_active) {
 #pragma unroll
@@ -333,6 +321,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
           }
         }
       }
+      for (nz = max(g, nz_s); nz < nz_e; ++nz) one(nz);
       nz = nz_e;
     }
     for (; nz < nz_e; ++nz) one(nz);
@@ -464,6 +453,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
 template <typename T, int VEC, int G, bool DIRECT, bool PERM = false, bool HOT = false>
 __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
   merge_tile<T, VEC, G, DIRECT, PERM, HOT>(a, blockIdx.x);
+}
+
+// The direct SpMV walk held to six resident 256-thread CTAs per SM (40 registers): the power-law
+// products it serves wait on their gathers, and a CTA more of warps in flight hides more of it.
+template <typename T, bool PERM, bool HOT>
+__global__ void __launch_bounds__(256, 6) merge_direct6_kernel(MergeArgs<T> a) {
+  merge_tile<T, 1, 1, true, PERM, HOT>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of
