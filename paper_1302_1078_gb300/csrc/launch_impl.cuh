@@ -190,9 +190,7 @@ cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, b
 template <typename T, int VEC, int G, bool DIRECT, bool PERM, bool HOT = false>
 static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
   auto kern = merge_kernel<T, VEC, G, DIRECT, PERM, HOT>;
-  if constexpr (DIRECT && VEC == 1 && G == 1) {
-    if (threads == 256) kern = merge_direct6_kernel<T, PERM, HOT>;
-  }
+  if constexpr (DIRECT && VEC == 1 && G == 1) kern = merge_direct6_kernel<T, PERM, HOT>;  // 40 registers
   const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

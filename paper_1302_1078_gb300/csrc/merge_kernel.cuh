@@ -455,8 +455,9 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
   merge_tile<T, VEC, G, DIRECT, PERM, HOT>(a, blockIdx.x);
 }
 
-// The direct SpMV walk held to six resident 256-thread CTAs per SM (40 registers): the power-law
-// products it serves wait on their gathers, and a CTA more of warps in flight hides more of it.
+// The direct SpMV walk held to 40 registers (six resident 256-thread CTAs per SM, or twelve of
+// 128 threads): the power-law products it serves wait on their gathers, and more warps in flight
+// hide more of it.
 template <typename T, bool PERM, bool HOT>
 __global__ void __launch_bounds__(256, 6) merge_direct6_kernel(MergeArgs<T> a) {
   merge_tile<T, 1, 1, true, PERM, HOT>(a, blockIdx.x);
