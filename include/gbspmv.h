@@ -83,9 +83,9 @@ typedef enum {
                                  whole row; k > 1: `lanes` lanes split the columns, as in ROWS;
                                  k == 1: one lane per row (lanes ignored).  Same results, bit
                                  for bit, as ROWS with lanes that split the columns (k > 1) or
-                                 with one lane per row (k == 1); for short rows and batched
-                                 items.  Values are not read through a permutation (not for the
-                                 backward pass's A^T) */
+                                 with one lane per row (k == 1); for short rows.  Not a
+                                 batched item form, and values are not read through a
+                                 permutation (not for the backward pass's A^T) */
 } gbs_variant;
 
 /*

@@ -1615,14 +1615,12 @@ std::vector<gbs_config> batch_candidates(const gbs_stats& st, int dtype, int k) 
     for (int l : {1, 2, 4, 8, 16, 32})
       if (l == 1 || st.mean_row >= 0.5 * l) add(GBS_VARIANT_ROWS, l, base_tile, 0);
     for (int it : {7, 15, 31}) add(GBS_VARIANT_MERGE, 0, 0, it);
-    add(GBS_VARIANT_ROWS_DIRECT, 1, 0, 0);
   } else {
     add(GBS_VARIANT_ROWS, 0, base_tile, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile / 2, 0);
     add(GBS_VARIANT_ROWS, 0, base_tile * 2, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 0);
     add(GBS_VARIANT_MERGE, 0, 0, 15);
-    add(GBS_VARIANT_ROWS_DIRECT, 0, 0, 0);
   }
   return c;
 }
@@ -1767,16 +1765,14 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
       gbs_config& g = given_cfgs[b];
       if (g.variant == GBS_VARIANT_AUTO) continue;
       int rc = GBS_OK;
-      if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE && g.variant != GBS_VARIANT_ROWS_DIRECT) {
-        rc = fail(GBS_EUNSUPPORTED,
-                  "item " + std::to_string(b) + ": batched configurations are ROWS, MERGE or ROWS_DIRECT");
+      if (g.variant != GBS_VARIANT_ROWS && g.variant != GBS_VARIANT_MERGE) {
+        rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": batched configurations are ROWS or MERGE");
       } else if (g.relabel != 0) {
         rc = fail(GBS_EUNSUPPORTED, "item " + std::to_string(b) + ": column relabelling is for plans of one matrix");
       } else {
         g.threads = kBatchThreads;
         g.emul = 0;
-        if ((g.variant == GBS_VARIANT_ROWS || g.variant == GBS_VARIANT_ROWS_DIRECT) && k > 1) g.lanes = p->G;
-        if (g.variant == GBS_VARIANT_ROWS_DIRECT && k == 1) g.lanes = 1;
+        if (g.variant == GBS_VARIANT_ROWS && k > 1) g.lanes = p->G;
         g = normalize(g, dtype);
         rc = check_cfg(g);
       }
@@ -1810,7 +1806,7 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
     if (tune && !given && it.m > 0) {
       float best = 1e30f;
       for (gbs_config cand : batch_candidates(st, dtype, k)) {
-        if (k > 1 && (cand.variant == GBS_VARIANT_ROWS || cand.variant == GBS_VARIANT_ROWS_DIRECT)) cand.lanes = p->G;
+        if (k > 1 && cand.variant == GBS_VARIANT_ROWS) cand.lanes = p->G;
         if (is_merge(cand.variant)) {
           // time the tile size the batch will run (capped to the shared-memory budget)
           const MergeGeom G = merge_geom(cand, it.m, it.nnz, dtype, k, vec16);
@@ -1850,13 +1846,7 @@ int spmv_csr_batched_plan_cfg(gbs_batch_plan** out, int nmat, const gbs_batch_it
     const gbs_batch_item& it = p->items[b];
     const gbs_config& c = p->cfgs[b];
     long long nitems = 0;
-    if (c.variant == GBS_VARIANT_ROWS_DIRECT) {
-      // no shared memory: one item per block of rows
-      const int lanes = k == 1 ? 1 : p->G;
-      p->cfgs[b].lanes = lanes;
-      const int rpc = kBatchThreads / lanes;
-      nitems = (it.m + rpc - 1) / rpc;
-    } else if (c.variant == GBS_VARIANT_ROWS) {
+    if (c.variant == GBS_VARIANT_ROWS) {
       const int lanes = k == 1 ? c.lanes : p->G;
       const int rpc = kBatchThreads / lanes;
       nitems = (it.m + rpc - 1) / rpc;
@@ -1985,7 +1975,7 @@ int spmv_csr_batched_looped(gbs_batch_plan* p, void* stream) {
     if (it.m == 0) continue;
     CsrView A{it.m, it.n, it.nnz, it.row_ptr, it.col_idx, it.vals};
     gbs_config c = p->cfgs[b];
-    if ((c.variant == GBS_VARIANT_ROWS || c.variant == GBS_VARIANT_ROWS_DIRECT) && p->k > 1) c.lanes = p->G;
+    if (c.variant == GBS_VARIANT_ROWS && p->k > 1) c.lanes = p->G;
     MergeBuffers mb = p->mbs[b];
     int rc = run_product(A, p->dtype, p->k, it.X, p->k == 1 ? 1 : it.ldx, it.Y, p->k == 1 ? 1 : it.ldy, c,
                          is_merge(c.variant) ? &mb : nullptr, true, s);

@@ -69,8 +69,9 @@ __device__ __forceinline__ MergeArgs<T> merge_args(const BatchDesc<T>& d) {
   return a;
 }
 
-// SPLIT (k == 1): ROWS lanes vary per matrix (ROWS_DIRECT: one lane per row).  !SPLIT (k > 1):
-// every matrix uses G column lanes.
+// SPLIT (k == 1): ROWS lanes vary per matrix.  !SPLIT (k > 1): every matrix uses G column lanes.
+// (ROWS_DIRECT items are not offered: they lost every whole-batch policy, and their code cost this
+// register-bound kernel spills.)
 template <typename T, int VEC, bool SPLIT, int G>
 __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __restrict__ descs, int nmat,
                                                       int total_items, int* __restrict__ next_item) {
@@ -95,13 +96,7 @@ __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __r
     }
     const BatchDesc<T> d = descs[lo];
     const int local = item - d.item_begin;
-    if (d.variant == GBS_VARIANT_ROWS_DIRECT) {
-      const RowsArgs<T> a = rows_args(d);
-      if constexpr (SPLIT)
-        rows_direct_block<T, 1, 1>(a, local);
-      else
-        rows_direct_block<T, VEC, G>(a, local);
-    } else if (d.variant == GBS_VARIANT_ROWS) {
+    if (d.variant == GBS_VARIANT_ROWS) {
       const RowsArgs<T> a = rows_args(d);
       if constexpr (SPLIT) {
         switch (d.lanes) {
@@ -134,10 +129,7 @@ __global__ void __launch_bounds__(256, 4) batched_kernel(const BatchDesc<T>* __r
     // every thread read s_item before the item's first internal barrier, and no thread reads
     // shared memory after the item's last barrier (ROWS: the last tile pass ends with one; MERGE:
     // the barrier before the completion count), so the next item's index is published, and the
-    // shared memory handed over, with a single barrier.  A ROWS_DIRECT item has no internal
-    // barrier and uses no shared memory: one barrier before the write of s_item makes sure every
-    // thread has read it.
-    if (d.variant == GBS_VARIANT_ROWS_DIRECT) __syncthreads();
+    // shared memory handed over, with a single barrier
     if (threadIdx.x == 0) s_item = claimed;
     __syncthreads();
   }

@@ -59,7 +59,7 @@ def test_batched_equals_looped_and_oracle(gbs, k, dtype, tune):
     ib = info["item_begin"]
     assert ib[0] == 0 and all(b >= a for a, b in zip(ib, ib[1:])) and ib[-1] == info["total_items"]
     variants = {c["variant"] for c in info["configs"]}
-    assert variants <= {1, 2, 5}
+    assert variants <= {1, 2}
     plan.run()
     torch.cuda.synchronize()
     batched = [y.clone() for y in Ys]
@@ -99,11 +99,11 @@ def test_batched_forced_merge_and_new_operands(gbs):
 @pytest.mark.parametrize("k,dtype", [(8, torch.float64), (1, torch.float64), (1, torch.float32)],
                          ids=["k8f64", "k1f64", "k1f32"])
 def test_batched_explicit_configs(gbs, k, dtype):
-    """Caller-given per-matrix configurations (ROWS / MERGE / ROWS_DIRECT / library's choice):
-    equal to the per-matrix loop bitwise and to the oracle; other variants are refused."""
+    """Caller-given per-matrix configurations (ROWS / MERGE / library's choice): equal to the
+    per-matrix loop bitwise and to the oracle; other variants are refused."""
     mats, Xs, Ys, host = make_batch(SMALL[:18], k, dtype, seed=9)
     cycle = [dict(variant=2, items=5), dict(variant=1, lanes=2, tile_nnz=96), None,
-             dict(variant=2, items=63), dict(variant=1, lanes=1, tile_nnz=4096), dict(variant=0), dict(variant=5)]
+             dict(variant=2, items=63), dict(variant=1, lanes=1, tile_nnz=4096), dict(variant=0)]
     cfgs = [cycle[b % len(cycle)] for b in range(len(mats))]
     plan = gbs.BatchedPlan(mats, Xs, Ys, configs=cfgs)
     info = plan.info()
@@ -120,8 +120,9 @@ def test_batched_explicit_configs(gbs, k, dtype):
     torch.cuda.synchronize()
     for b in range(len(Ys)):
         assert torch.equal(Ys[b], batched[b]), f"batched != looped for matrix {b}"
-    with pytest.raises(gbs._capi.GbsError):
-        gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=3), None])
+    for v in (3, 4, 5):  # ROWS_TMA, MERGE_DIRECT and ROWS_DIRECT are not batch item forms
+        with pytest.raises(gbs._capi.GbsError):
+            gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=v), None])
     with pytest.raises(gbs._capi.GbsError):  # tile below 32 nonzeros
         gbs.BatchedPlan(mats[:2], Xs[:2], Ys[:2], configs=[dict(variant=1, tile_nnz=16), None])
     if k == 1:  # lanes per row must be a power of two (k > 1 uses the batch's column lanes)
