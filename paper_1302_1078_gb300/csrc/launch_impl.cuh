@@ -2,6 +2,7 @@
 // kernels_f64.cu / kernels_f32.cu so that the two compile in parallel.
 #pragma once
 #include <algorithm>
+#include <atomic>
 
 #include "launch.h"
 #include "merge_kernel.cuh"
@@ -16,10 +17,74 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The SM's 256 KB of unified storage is split between shared memory and L1.  Left to itself the
+// driver sizes the shared part for as many CTAs as the thread limit admits (64 KB for the direct
+// merge walk, which uses a few hundred bytes), and what it takes is lost to L1, where these
+// kernels' gathers of x hit.  prefer_l1 asks for the smallest split that still holds every CTA
+// that can be resident: an upper bound on that count from the thread, block and register limits
+// (register allocation rounded to 256 per warp), times the CTA's dynamic shared memory plus the
+// 1 KB the system reserves per CTA.  The bound can only over-count, so the split never limits
+// occupancy.  The device's limits are read once per process (the library serves one kind of GPU);
+// each kernel keeps its register count and the split it last asked for on which device, so a
+// repeated launch makes no extra runtime call.
+struct SmLimits {
+  int per_sm = 0, reserved = 0, thr_sm = 0, blk_sm = 0, regs_sm = 0;
+  cudaError_t err = cudaSuccess;
+};
+static const SmLimits& sm_limits() {
+  static const SmLimits lim = [] {
+    SmLimits l;
+    int dev = 0;
+    l.err = cudaGetDevice(&dev);
+    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    return l;
+  }();
+  return lim;
+}
+
+struct L1Split {
+  std::atomic<int> regs{0};
+  std::atomic<int> last{-1};  // (device << 8) | percentage last set
+};
+
+template <typename K>
+static cudaError_t prefer_l1(K kernel, int threads, size_t smem, L1Split& st) {
+  const SmLimits& l = sm_limits();
+  if (l.err != cudaSuccess) return l.err;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int r = st.regs.load(std::memory_order_relaxed);
+  if (r <= 0) {
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    r = fa.numRegs > 0 ? fa.numRegs : 1;
+    st.regs.store(r, std::memory_order_relaxed);
+  }
+  const int warps = (threads + 31) / 32;
+  const long long per_warp = ((long long)r * 32 + 255) / 256 * 256;
+  long long ctas = std::min<long long>(l.thr_sm / threads, l.blk_sm);
+  ctas = std::min<long long>(ctas, l.regs_sm / (per_warp * warps));
+  ctas = std::max<long long>(ctas, 1);
+  const long long need = ctas * ((long long)smem + l.reserved);
+  const int pct = l.per_sm > 0 ? (int)std::min<long long>(100, (need * 100 + l.per_sm - 1) / l.per_sm) : 100;
+  const int tag = (dev << 8) | pct;
+  if (st.last.load(std::memory_order_relaxed) == tag) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess) return e;
+  st.last.store(tag, std::memory_order_relaxed);
+  return cudaSuccess;
+}
+
 template <typename T, int VEC, int LANES, bool SPLIT, bool PERM>
 static cudaError_t rows_go(const RowsArgs<T>& a, int grid, int threads, size_t smem, cudaStream_t s) {
   auto kern = rows_kernel<T, VEC, LANES, SPLIT, PERM>;
+  static L1Split split;
   cudaError_t e = set_smem(kern, smem);
+  if (e == cudaSuccess) e = prefer_l1(kern, threads, smem, split);
   if (e != cudaSuccess) return e;
   kern<<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
@@ -71,6 +136,9 @@ cudaError_t launch_rows_t(const CsrView& A, const DenseView& D, int lanes, bool 
 
 template <typename T, int VEC, int LANES>
 static cudaError_t rows_direct_go(const RowsArgs<T>& a, int grid, int threads, cudaStream_t s) {
+  static L1Split split;
+  const cudaError_t e = prefer_l1(rows_direct_kernel<T, VEC, LANES>, threads, 0, split);
+  if (e != cudaSuccess) return e;
   rows_direct_kernel<T, VEC, LANES><<<grid, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -192,7 +260,9 @@ static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) 
   auto kern = merge_kernel<T, VEC, G, DIRECT, PERM, HOT>;
   if constexpr (DIRECT && VEC == 1 && G == 1) kern = merge_direct6_kernel<T, PERM, HOT>;  // 40 registers
   const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
+  static L1Split split;
   cudaError_t e = set_smem(kern, smem);
+  if (e == cudaSuccess) e = prefer_l1(kern, threads, smem, split);
   if (e != cudaSuccess) return e;
   kern<<<a.ctas, threads, smem, s>>>(a);
   e = cudaGetLastError();

@@ -101,7 +101,7 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
   size_t b = DIRECT ? 0 : ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;  // s_val
   size_t c = DIRECT ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;  // s_col
   size_t d = 2 * 32 * sizeof(int);                                   // s_wkey, s_cinkey
-  size_t e = 2 * (size_t)threads * VEC * sizeof(T);                  // s_wval, s_cinval (per warp: 32 lanes x VEC)
+  size_t e = 2 * (size_t)(threads / 32) * G * VEC * sizeof(T);       // s_wval, s_cinval (per warp: G lanes x VEC)
   return a + b + c + d + e;
 }
 
@@ -128,8 +128,8 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   int* s_wkey = reinterpret_cast<int*>(smem_raw + off);
   int* s_cinkey = s_wkey + 32;
   off += 2 * 32 * sizeof(int);
-  T* s_wval = reinterpret_cast<T*>(smem_raw + off);      // [nw][32 * VEC]
-  T* s_cinval = s_wval + (size_t)blockDim.x * VEC;       // [nw][32 * VEC]
+  T* s_wval = reinterpret_cast<T*>(smem_raw + off);      // [nw][G * VEC]
+  T* s_cinval = s_wval + (size_t)nw * G * VEC;           // [nw][G * VEC]
 
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
@@ -386,7 +386,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   if (mt == MT - 1) {
     if (lane == 0) s_wkey[w] = key;
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) s_wval[((size_t)w * 32 + lane) * VEC + j] = S[j];
+    for (int j = 0; j < VEC; ++j) s_wval[((size_t)w * G + lane) * VEC + j] = S[j];
   }
   __syncthreads();
   // carry into warp ww: the run of the previous warp's last key, chained over whole-warp runs
@@ -398,7 +398,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
       const int k_prev = s_wkey[ww - 1];
       T nv[VEC];
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) nv[j] = s_wval[((size_t)(ww - 1) * 32 + c) * VEC + j];
+      for (int j = 0; j < VEC; ++j) nv[j] = s_wval[((size_t)(ww - 1) * G + c) * VEC + j];
       if (ww >= 2 && cin_key == k_prev) {
 #pragma unroll
         for (int j = 0; j < VEC; ++j) nv[j] += cin[j];
@@ -406,7 +406,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
 #pragma unroll
       for (int j = 0; j < VEC; ++j) {
         cin[j] = nv[j];
-        s_cinval[((size_t)ww * 32 + c) * VEC + j] = nv[j];
+        s_cinval[((size_t)ww * G + c) * VEC + j] = nv[j];
       }
       cin_key = k_prev;
       if (c == 0) s_cinkey[ww] = k_prev;
@@ -420,7 +420,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     if (__any_sync(0xffffffffu, take)) {
 #pragma unroll
       for (int j = 0; j < VEC; ++j)
-        if (take) S[j] += s_cinval[((size_t)w * 32 + lane) * VEC + j];
+        if (take) S[j] += s_cinval[((size_t)w * G + lane) * VEC + j];
     }
   }
   // finish the split head row with the run that ends just before this merge thread
@@ -432,7 +432,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     if (mt == 0) {
       pkey = w > 0 ? wkey : -1;
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) ps[j] = w > 0 ? s_cinval[((size_t)w * 32 + lane) * VEC + j] : T(0);
+      for (int j = 0; j < VEC; ++j) ps[j] = w > 0 ? s_cinval[((size_t)w * G + lane) * VEC + j] : T(0);
     }
     const bool take = head_row >= 0 && pkey == head_row;
     if (__any_sync(0xffffffffu, take)) {
