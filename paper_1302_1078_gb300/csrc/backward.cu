@@ -1,11 +1,12 @@
 // Backward pass of Y = A X with respect to the stored values (the paper has
 // no backward pass): the sampled dense-dense product over A's pattern
 //   dvals[p] = sum_c dY[row(p), c] * X[col_idx[p], c].
-// One thread per nonzero sums its k products in column order, so no FP64
-// reduction across lanes is needed (on GB300 every FP64 instruction counts);
-// consecutive threads hold consecutive nonzeros, so their dY rows are mostly
-// the same row (served by L1) and their col_idx/row reads are coalesced.
-// The X rows are gathered with the L2 evict-last policy, like SpMM.
+// Each lane of a warp takes U nonzeros 32 apart (the warp covers 32 * U consecutive ones) and
+// sums each one's k products in column order, so no FP64 reduction across lanes is needed (on
+// GB300 every FP64 instruction counts).  Every id load and dvals store of the warp is 32
+// consecutive elements, and a lane's U gathers are independent, so U are in flight per lane;
+// neighbouring nonzeros mostly share their dY row (served by L1).  The X rows are gathered with the
+// L2 evict-last policy, like SpMM.
 #include <algorithm>
 #include <cstdint>
 
@@ -15,30 +16,73 @@
 
 namespace gbs {
 
-template <typename T, int VEC>
+template <typename T, int VEC, int U, bool K1>
 __global__ void __launch_bounds__(256) sddmm_kernel(int nnz, int k, const int* __restrict__ rows,
                                                     const int* __restrict__ col_idx, const T* __restrict__ X,
                                                     long long ldx, const T* __restrict__ dY, long long lddy,
                                                     T* __restrict__ dvals) {
   const uint64_t pol_keep = policy_evict_last();
   const uint64_t pol_stream = policy_evict_first();
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) {
-    const int i = ld_stream(rows + p, pol_stream);
-    const int j = ld_stream(col_idx + p, pol_stream);
-    const T* __restrict__ xr = X + (long long)j * ldx;
-    const T* __restrict__ yr = dY + (long long)i * lddy;
-    Acc<T> acc;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long step = ((long long)gridDim.x * blockDim.x >> 5) * 32 * U;
+  for (long long base = warp * 32 * U; base < nnz; base += step) {
+    long long p[U];
+    bool in[U];
+    int iu[U], ju[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      p[u] = base + 32 * u + lane;
+      in[u] = p[u] < nnz;
+      iu[u] = in[u] ? ld_stream(rows + p[u], pol_stream) : 0;
+      ju[u] = in[u] ? ld_stream(col_idx + p[u], pol_stream) : 0;
+    }
+    Acc<T> acc[U];
     int c = 0;
+    if constexpr (K1) {
+      T xs[U], ys[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (in[u]) {
+          xs[u] = ld_keep(X + ju[u], pol_keep);
+          ys[u] = ld_keep(dY + iu[u], pol_keep);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u].add(ys[u], xs[u]);
+      c = k;
+    }
     if constexpr (VEC > 1) {
       for (; c + VEC <= k; c += VEC) {
-        Vec<T, VEC> xv = ld_keep_vec<T, VEC>(xr + c, pol_keep);
-        Vec<T, VEC> yv = ld_keep_vec<T, VEC>(yr + c, pol_keep);
+        Vec<T, VEC> xv[U], yv[U];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) acc.add(yv.v[q], xv.v[q]);
+        for (int u = 0; u < U; ++u) {
+          if (in[u]) {
+            xv[u] = ld_keep_vec<T, VEC>(X + (long long)ju[u] * ldx + c, pol_keep);
+            yv[u] = ld_keep_vec<T, VEC>(dY + (long long)iu[u] * lddy + c, pol_keep);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[u].add(yv[u].v[q], xv[u].v[q]);
       }
     }
-    for (; c < k; ++c) acc.add(ld_keep(yr + c, pol_keep), ld_keep(xr + c, pol_keep));
-    st_stream(dvals + p, acc.value());
+    for (; c < k; ++c) {
+      T xs[U], ys[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (in[u]) {
+          xs[u] = ld_keep(X + (long long)ju[u] * ldx + c, pol_keep);
+          ys[u] = ld_keep(dY + (long long)iu[u] * lddy + c, pol_keep);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u].add(ys[u], xs[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (in[u]) st_stream(dvals + p[u], acc[u].value());
   }
 }
 
@@ -49,13 +93,17 @@ static cudaError_t sddmm_t(int nnz, int k, const int* rows, const int* col_idx, 
   constexpr int V = 16 / (int)sizeof(T);
   const bool vec = k >= V && (reinterpret_cast<uintptr_t>(X) % 16 == 0) && (reinterpret_cast<uintptr_t>(dY) % 16 == 0) &&
                    (ldx * (long long)sizeof(T)) % 16 == 0 && (lddy * (long long)sizeof(T)) % 16 == 0;
-  const int grid = (int)std::min<long long>(152LL * 16, (nnz + 255) / 256);
-  if (vec)
-    sddmm_kernel<T, V><<<grid, 256, 0, s>>>(nnz, k, rows, col_idx, static_cast<const T*>(X), ldx,
-                                            static_cast<const T*>(dY), lddy, static_cast<T*>(dvals));
+  constexpr int U = 2;  // nonzeros per lane (four measured no faster; the dot products are the same)
+  const int grid = (int)std::min<long long>(152LL * 16, ((long long)nnz + U * 256 - 1) / (U * 256));
+  const T* x = static_cast<const T*>(X);
+  const T* dy = static_cast<const T*>(dY);
+  T* dv = static_cast<T*>(dvals);
+  if (k == 1)
+    sddmm_kernel<T, 1, U, true><<<grid, 256, 0, s>>>(nnz, k, rows, col_idx, x, 1, dy, 1, dv);
+  else if (vec)
+    sddmm_kernel<T, V, U, false><<<grid, 256, 0, s>>>(nnz, k, rows, col_idx, x, ldx, dy, lddy, dv);
   else
-    sddmm_kernel<T, 1><<<grid, 256, 0, s>>>(nnz, k, rows, col_idx, static_cast<const T*>(X), ldx,
-                                            static_cast<const T*>(dY), lddy, static_cast<T*>(dvals));
+    sddmm_kernel<T, 1, U, false><<<grid, 256, 0, s>>>(nnz, k, rows, col_idx, x, ldx, dy, lddy, dv);
   return cudaGetLastError();
 }
 
