@@ -90,10 +90,11 @@ WORKLOAD_TEXT = {
 # Source files that define each variant's kernel: a DRAM-traffic figure recorded from an ncu
 # capture (profiles/traffic.txt) is reported only while these files are unchanged.
 KERNEL_SOURCES = {
-    1: ["rows_kernel.cuh", "device_common.cuh"],
-    2: ["merge_kernel.cuh", "device_common.cuh"],
-    3: ["rows_tma.cuh", "rows_kernel.cuh", "device_common.cuh", "df64.cuh"],
-    4: ["merge_kernel.cuh", "device_common.cuh"],
+    1: ["rows_kernel.cuh", "device_common.cuh", "launch_impl.cuh"],
+    2: ["merge_kernel.cuh", "device_common.cuh", "launch_impl.cuh"],
+    3: ["rows_tma.cuh", "rows_kernel.cuh", "device_common.cuh", "df64.cuh", "launch_impl.cuh"],
+    4: ["merge_kernel.cuh", "device_common.cuh", "launch_impl.cuh"],
+    5: ["rows_kernel.cuh", "device_common.cuh", "launch_impl.cuh"],
 }
 
 

@@ -1554,7 +1554,7 @@ size_t merge_smem_host(int dtype, int g, bool vec16, int items, bool direct) {
   size_t a = direct ? 0 : ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;
   size_t b = direct ? 0 : ((ipc + 4) * es + 15) & ~(size_t)15;
   size_t c = direct ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
-  return a + b + c + 2 * 32 * sizeof(int) + 2 * (size_t)(kBatchThreads / 32) * g * vec * es;
+  return a + b + c + 2 * (size_t)(kBatchThreads / 32) * sizeof(int) + 2 * (size_t)(kBatchThreads / 32) * g * vec * es;
 }
 
 template <typename T>

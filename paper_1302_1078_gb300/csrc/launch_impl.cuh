@@ -18,17 +18,21 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // The SM's 256 KB of unified storage is split between shared memory and L1.  Left to itself the
-// driver sizes the shared part for as many CTAs as the thread limit admits (64 KB for the direct
-// merge walk, which uses a few hundred bytes), and what it takes is lost to L1, where these
-// kernels' gathers of x hit.  prefer_l1 asks for the smallest split that still holds every CTA
-// that can be resident: an upper bound on that count from the thread, block and register limits
-// (register allocation rounded to 256 per warp), times the CTA's dynamic shared memory plus the
-// 1 KB the system reserves per CTA.  The bound can only over-count, so the split never limits
-// occupancy.  The device's limits are read once per process (the library serves one kind of GPU);
-// each kernel keeps its register count and the split it last asked for on which device, so a
-// repeated launch makes no extra runtime call.
+// driver sizes the shared part for the 32 CTAs an SM can hold at most (64 KB for the direct merge
+// walk, which uses a few hundred bytes per CTA), and what it takes is lost to L1, where these
+// kernels' gathers of x hit.  The carveout attribute is only a hint, and the driver maps it to a
+// configuration in its own way; measured on GB300 (one probe kernel, ncu's
+// launch__shared_mem_config_size): hint 0 gives 8 KB, 1 gives 16 KB, 2 and 3 give 32 KB, 4 to 7
+// the default 64 KB, and the driver keeps the small ones even where they limit occupancy.
+// prefer_l1 therefore picks the smallest of 8, 16 and 32 KB that holds every CTA that can be
+// resident: an upper bound on that count from the thread, block and register limits (register
+// allocation rounded to 256 per warp), times the CTA's dynamic shared memory (rounded up to 256
+// bytes) plus the 1 KB the system reserves per CTA; above 32 KB it leaves the driver's default.
+// The bound can only over-count, so the split never limits occupancy.  The device's limits are
+// read once per process (the library serves one kind of GPU); each kernel keeps its register
+// count and the hint it last set on which device, so a repeated launch makes no extra runtime call.
 struct SmLimits {
-  int per_sm = 0, reserved = 0, thr_sm = 0, blk_sm = 0, regs_sm = 0;
+  int reserved = 0, thr_sm = 0, blk_sm = 0, regs_sm = 0;
   cudaError_t err = cudaSuccess;
 };
 static const SmLimits& sm_limits() {
@@ -36,7 +40,6 @@ static const SmLimits& sm_limits() {
     SmLimits l;
     int dev = 0;
     l.err = cudaGetDevice(&dev);
-    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
     if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
@@ -48,7 +51,7 @@ static const SmLimits& sm_limits() {
 
 struct L1Split {
   std::atomic<int> regs{0};
-  std::atomic<int> last{-1};  // (device << 8) | percentage last set
+  std::atomic<int> last{-1};  // (device << 8) | (hint & 0xff) last set
 };
 
 template <typename K>
@@ -70,9 +73,9 @@ static cudaError_t prefer_l1(K kernel, int threads, size_t smem, L1Split& st) {
   long long ctas = std::min<long long>(l.thr_sm / threads, l.blk_sm);
   ctas = std::min<long long>(ctas, l.regs_sm / (per_warp * warps));
   ctas = std::max<long long>(ctas, 1);
-  const long long need = ctas * ((long long)smem + l.reserved);
-  const int pct = l.per_sm > 0 ? (int)std::min<long long>(100, (need * 100 + l.per_sm - 1) / l.per_sm) : 100;
-  const int tag = (dev << 8) | pct;
+  const long long need = ctas * ((((long long)smem + 255) & ~255LL) + l.reserved);  // 256-byte allocation units
+  const int pct = need <= 8 * 1024 ? 0 : need <= 16 * 1024 ? 1 : need <= 32 * 1024 ? 2 : (int)cudaSharedmemCarveoutDefault;
+  const int tag = (dev << 8) | (pct & 0xff);
   if (st.last.load(std::memory_order_relaxed) == tag) return cudaSuccess;
   if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess) return e;
   st.last.store(tag, std::memory_order_relaxed);

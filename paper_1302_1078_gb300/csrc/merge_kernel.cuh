@@ -100,7 +100,7 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
   size_t a = DIRECT ? 0 : ((ipc + 2) * sizeof(int) + 15) & ~(size_t)15;  // s_rp
   size_t b = DIRECT ? 0 : ((ipc + 4) * sizeof(T) + 15) & ~(size_t)15;  // s_val
   size_t c = DIRECT ? 0 : ((ipc + 4) * sizeof(int) + 15) & ~(size_t)15;  // s_col
-  size_t d = 2 * 32 * sizeof(int);                                   // s_wkey, s_cinkey
+  size_t d = 2 * (size_t)(threads / 32) * sizeof(int);               // s_wkey, s_cinkey (per warp)
   size_t e = 2 * (size_t)(threads / 32) * G * VEC * sizeof(T);       // s_wval, s_cinval (per warp: G lanes x VEC)
   return a + b + c + d + e;
 }
@@ -125,9 +125,9 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   if (!DIRECT) off += (((size_t)ipc + 4) * sizeof(T) + 15) & ~(size_t)15;
   int* s_col = reinterpret_cast<int*>(smem_raw + off);
   if (!DIRECT) off += (((size_t)ipc + 4) * sizeof(int) + 15) & ~(size_t)15;
-  int* s_wkey = reinterpret_cast<int*>(smem_raw + off);
-  int* s_cinkey = s_wkey + 32;
-  off += 2 * 32 * sizeof(int);
+  int* s_wkey = reinterpret_cast<int*>(smem_raw + off);  // [nw]
+  int* s_cinkey = s_wkey + nw;                            // [nw]
+  off += 2 * (size_t)nw * sizeof(int);
   T* s_wval = reinterpret_cast<T*>(smem_raw + off);      // [nw][G * VEC]
   T* s_cinval = s_wval + (size_t)nw * G * VEC;           // [nw][G * VEC]
 
