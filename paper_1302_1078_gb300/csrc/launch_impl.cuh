@@ -186,18 +186,44 @@ cudaError_t launch_rows_direct_t(const CsrView& A, const DenseView& D, int lanes
   }
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT, int EMUL>
-static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* status, int threads, size_t smem,
-                               cudaStream_t s) {
-  auto kern = rows_tma_kernel<T, VEC, LANES, SPLIT, EMUL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// The persistent grid (resident CTAs per SM x SMs) and the shared-memory attribute are worked out
+// once per kernel, block size and shared-memory size on a device and kept, so that a repeated
+// launch makes no runtime query between the caller's events and the kernel.
+struct GridCache {
+  std::atomic<long long> key{-1};  // (device << 48) | (threads << 32) | smem
+  std::atomic<int> grid_cap{0};    // resident CTAs per SM x SMs
+};
+
+template <typename K>
+static cudaError_t persistent_cap(K kern, int threads, size_t smem, GridCache& gc, int* cap) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int bps = 0, dev = 0, sms = 0;
+  const long long key = ((long long)dev << 48) | ((long long)threads << 32) | (long long)smem;
+  if (gc.key.load(std::memory_order_acquire) == key) {
+    *cap = gc.grid_cap.load(std::memory_order_relaxed);
+    return cudaSuccess;
+  }
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  int bps = 0, sms = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem)) != cudaSuccess) return e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if (bps < 1) return cudaErrorInvalidConfiguration;
-  const int grid = std::min(nblocks, bps * sms);
+  *cap = bps * sms;
+  gc.grid_cap.store(*cap, std::memory_order_relaxed);
+  gc.key.store(key, std::memory_order_release);
+  return cudaSuccess;
+}
+
+template <typename T, int VEC, int LANES, bool SPLIT, int EMUL, bool UNIT = false>
+static cudaError_t rows_tma_go(const RowsArgs<T>& a, int nblocks, int nnz, int* status, int threads, size_t smem,
+                               cudaStream_t s) {
+  auto kern = rows_tma_kernel<T, VEC, LANES, SPLIT, EMUL, UNIT>;
+  static GridCache gc;
+  int cap = 0;
+  const cudaError_t e = persistent_cap(kern, threads, smem, gc, &cap);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(nblocks, cap);
   kern<<<grid, threads, smem, s>>>(a, nblocks, nnz, status);
   return cudaGetLastError();
 }
@@ -213,6 +239,8 @@ static cudaError_t rows_tma_emul(const RowsArgs<T>& a, int emul, int nblocks, in
       default: break;
     }
   }
+  if constexpr (SPLIT && VEC == 1)
+    if (a.ldx == 1 && a.ldy == 1) return rows_tma_go<T, 1, LANES, true, 0, true>(a, nblocks, nnz, status, threads, smem, s);
   return rows_tma_go<T, VEC, LANES, SPLIT, 0>(a, nblocks, nnz, status, threads, smem, s);
 }
 
@@ -261,11 +289,15 @@ cudaError_t launch_rows_tma_t(const CsrView& A, const DenseView& D, int lanes, b
 template <typename T, int VEC, int G, bool DIRECT, bool PERM, bool HOT = false>
 static cudaError_t merge_go(const MergeArgs<T>& a, int threads, cudaStream_t s) {
   auto kern = merge_kernel<T, VEC, G, DIRECT, PERM, HOT>;
-  if constexpr (DIRECT && VEC == 1 && G == 1) kern = merge_direct6_kernel<T, PERM, HOT>;  // 40 registers
+  static L1Split split, split_k1;
+  bool k1 = false;
+  if constexpr (DIRECT && VEC == 1 && G == 1) {  // 40 registers; its own form for SpMV with contiguous x, y
+    k1 = a.k == 1 && a.ldx == 1 && a.ldy == 1;
+    kern = k1 ? merge_direct6_kernel<T, PERM, HOT, true> : merge_direct6_kernel<T, PERM, HOT, false>;
+  }
   const size_t smem = merge_smem_bytes<T, VEC, G, DIRECT>(threads, a.items);
-  static L1Split split;
   cudaError_t e = set_smem(kern, smem);
-  if (e == cudaSuccess) e = prefer_l1(kern, threads, smem, split);
+  if (e == cudaSuccess) e = prefer_l1(kern, threads, smem, k1 ? split_k1 : split);
   if (e != cudaSuccess) return e;
   kern<<<a.ctas, threads, smem, s>>>(a);
   e = cudaGetLastError();

@@ -107,9 +107,13 @@ __host__ __device__ inline size_t merge_smem_bytes(int threads, int items) {
 
 // One merge-path tile b of the product (the whole CTA works on it).  Used by the
 // standalone kernel below and by the batched persistent kernel.
-template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false, bool HOT = false>
+template <typename T, int VEC, int G, bool DIRECT = false, bool PERM = false, bool HOT = false, bool K1 = false>
 __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   static_assert(!HOT || (DIRECT && VEC == 1), "the hot-column policy is for the direct form's scalar gathers");
+  static_assert(!K1 || (VEC == 1 && G == 1), "the SpMV form has one column and one lane per merge thread");
+  // K1: SpMV (k == 1) with contiguous x and y, so their strides drop out of every address
+  const int kk = K1 ? 1 : a.k;
+  const long long ldx = K1 ? 1 : a.ldx, ldy = K1 ? 1 : a.ldy;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nt = blockDim.x / G;
   const int nw = blockDim.x / 32;
@@ -164,8 +168,8 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   constexpr int MT = 32 / G;                // merge threads per warp
   const int mt = wl / G;                    // merge thread inside the warp
   const int c_lo = lane * VEC;
-  const bool col_active = c_lo < a.k;
-  const bool col_full = c_lo + VEC <= a.k;
+  const bool col_active = c_lo < kk;
+  const bool col_full = c_lo + VEC <= kk;
 
   // this merge thread's share of the tile: diagonals [ds, de) relative to d0, each located by a
   // binary search of the window; the two searches step together so their reads overlap
@@ -203,11 +207,11 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
   const T* __restrict__ Xc = a.X + c_lo;
 
   auto store_row = [&](int r, const T* out) {
-    T* yr = a.Y + (long long)r * a.ldy + c_lo;
+    T* yr = a.Y + (long long)r * ldy + c_lo;
     if (col_full)
       st_stream_vec<T, VEC>(yr, out);
     else
-      for (int j = 0; j < a.k - c_lo; ++j) st_stream(yr + j, out[j]);
+      for (int j = 0; j < kk - c_lo; ++j) st_stream(yr + j, out[j]);
   };
   auto emit = [&](int r) {
     T out[VEC];
@@ -231,13 +235,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     auto gather = [&](int c) {
       Vec<T, VEC> xv;
       if constexpr (HOT) {
-        xv.v[0] = c < a.hot_cols ? ld_keep(Xc + (long long)c * a.ldx, pol_keep)
-                                 : ld_keep_na(Xc + (long long)c * a.ldx, pol_keep);
+        xv.v[0] = c < a.hot_cols ? ld_keep(Xc + (long long)c * ldx, pol_keep)
+                                 : ld_keep_na(Xc + (long long)c * ldx, pol_keep);
       } else if (col_full) {
-        xv = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
+        xv = ld_keep_vec<T, VEC>(Xc + (long long)c * ldx, pol_keep);
       } else {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) xv.v[j] = (c_lo + j < a.k) ? ld_keep(Xc + (long long)c * a.ldx + j, pol_keep) : T(0);
+        for (int j = 0; j < VEC; ++j) xv.v[j] = (c_lo + j < kk) ? ld_keep(Xc + (long long)c * ldx + j, pol_keep) : T(0);
       }
       return xv;
     };
@@ -337,10 +341,10 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
         v[u] = s_val[nz + u - a0];
         const int c = s_col[nz + u - a0];
         if (col_full) {
-          xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c * a.ldx, pol_keep);
+          xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c * ldx, pol_keep);
         } else {
 #pragma unroll
-          for (int j = 0; j < VEC; ++j) xv[u].v[j] = (c_lo + j < a.k) ? ld_keep(Xc + (long long)c * a.ldx + j, pol_keep) : T(0);
+          for (int j = 0; j < VEC; ++j) xv[u].v[j] = (c_lo + j < kk) ? ld_keep(Xc + (long long)c * ldx + j, pol_keep) : T(0);
         }
       }
     }
@@ -446,7 +450,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs<T>& a, int b) {
     // CTA carry: run sum of the row still open at the tile's end
     if (lane == 0) a.carry_row[b] = key < a.m ? key : -1;
     if (col_active)
-      for (int j = 0; j < VEC && c_lo + j < a.k; ++j) a.carry_val[(size_t)b * a.k + c_lo + j] = S[j];
+      for (int j = 0; j < VEC && c_lo + j < kk; ++j) a.carry_val[(size_t)b * kk + c_lo + j] = S[j];
   }
 }
 
@@ -458,9 +462,9 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs<T> a) {
 // The direct SpMV walk held to 40 registers (six resident 256-thread CTAs per SM, or twelve of
 // 128 threads): the power-law products it serves wait on their gathers, and more warps in flight
 // hide more of it.
-template <typename T, bool PERM, bool HOT>
+template <typename T, bool PERM, bool HOT, bool K1>
 __global__ void __launch_bounds__(256, 6) merge_direct6_kernel(MergeArgs<T> a) {
-  merge_tile<T, 1, 1, true, PERM, HOT>(a, blockIdx.x);
+  merge_tile<T, 1, 1, true, PERM, HOT, K1>(a, blockIdx.x);
 }
 
 // Adds the CTA carries to the rows they belong to: the first CTA of each run of

@@ -102,8 +102,11 @@ __host__ __device__ inline size_t rows_tma_smem_bytes(int rpc, int tile) {
   return bars + rp + 2 * (val + col);
 }
 
-template <typename T, int VEC, int LANES, bool SPLIT, int EMUL>
+// UNIT (SpMV with contiguous x and y): the strides are 1 and drop out of every address.
+template <typename T, int VEC, int LANES, bool SPLIT, int EMUL, bool UNIT = false>
 __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblocks, int nnz, int* __restrict__ status) {
+  static_assert(!UNIT || (SPLIT && VEC == 1), "unit strides are the SpMV form's");
+  const long long ldx = UNIT ? 1 : a.ldx, ldy = UNIT ? 1 : a.ldy;
   static_assert(EMUL == 0 || sizeof(T) == 8, "FP32-pipe emulation is for double values");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpc = blockDim.x / LANES;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           }
           sum += (T)e.value();
         }
-        st_stream(a.Y + (long long)(bj * rpc + tid) * a.ldy, sum);
+        st_stream(a.Y + (long long)(bj * rpc + tid) * ldy, sum);
       }
     }
   };
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
             c[u] = sc[p + (q0 + u) * STEP - a0];
           }
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep(Xc + (long long)c[u] * a.ldx, pol_keep);
+          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep(Xc + (long long)c[u] * ldx, pol_keep);
         };
         int egroups = 0;
         auto fma4 = [&](const T* v, const T* x) {
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
         for (int u = 0; u < kUnroll - 1; ++u)
           if (u < rem) {
             vb[u] = sv[p + (q0 + u) * STEP - a0];
-            xb[u] = ld_keep(Xc + (long long)sc[p + (q0 + u) * STEP - a0] * a.ldx, pol_keep);
+            xb[u] = ld_keep(Xc + (long long)sc[p + (q0 + u) * STEP - a0] * ldx, pol_keep);
           }
         // A guarded product would be computed on every lane and kept by a select (a multiply-add
         // has no side effects, so the compiler may lift it out of its branch).  For double values
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
             c[u] = sc[p + q0 + u - a0];
           }
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
+          for (int u = 0; u < kUnroll; ++u) x[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * ldx, pol_keep);
         };
         auto fma4 = [&](const T* v, const Vec<T, VEC>* x) {
 #pragma unroll
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           }
         }
         for (int q = full * kUnroll; q < cnt; ++q) {
-          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p + q - a0] * a.ldx, pol_keep);
+          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p + q - a0] * ldx, pol_keep);
 #pragma unroll
           for (int j = 0; j < VEC; ++j) acc[j].add(sv[p + q - a0], xv.v[j]);
         }
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           }
           Vec<T, VEC> xv[kUnroll];
 #pragma unroll
-          for (int u = 0; u < kUnroll; ++u) xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * a.ldx, pol_keep);
+          for (int u = 0; u < kUnroll; ++u) xv[u] = ld_keep_vec<T, VEC>(Xc + (long long)c[u] * ldx, pol_keep);
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
             if constexpr (EMUL > 0) {
@@ -450,14 +453,14 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
           for (int j = 0; j < VEC; ++j) acc[j].add_partial((T)eacc[j].value());
         }
         for (; p < re; p += STEP) {
-          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p - a0] * a.ldx, pol_keep);
+          Vec<T, VEC> xv = ld_keep_vec<T, VEC>(Xc + (long long)sc[p - a0] * ldx, pol_keep);
 #pragma unroll
           for (int j = 0; j < VEC; ++j) acc[j].add(sv[p - a0], xv.v[j]);
         }
       } else {
         const int nv = a.k - c_lo;
         for (; p < re; p += STEP) {
-          const T* xr = Xc + (long long)sc[p - a0] * a.ldx;
+          const T* xr = Xc + (long long)sc[p - a0] * ldx;
 #pragma unroll
           for (int j = 0; j < VEC; ++j)
             if (j < nv) acc[j].add(sv[p - a0], ld_keep(xr + j, pol_keep));
@@ -469,13 +472,13 @@ __global__ void __launch_bounds__(256) rows_tma_kernel(RowsArgs<T> a, int nblock
       s_red[st * 256 + tid] = acc[0].value();
       if constexpr (EMUL > 0) s_redf[st * 256 + tid] = make_float2(eacc[0].s, eacc[0].c);
     } else if constexpr (SPLIT) {
-      if (active) st_stream(a.Y + (long long)(r0 + g) * a.ldy, acc[0].value());
+      if (active) st_stream(a.Y + (long long)(r0 + g) * ldy, acc[0].value());
     } else {
       if (active && col_active) {
         T out[VEC];
 #pragma unroll
         for (int j = 0; j < VEC; ++j) out[j] = acc[j].value();
-        T* yr = a.Y + (long long)(r0 + g) * a.ldy + c_lo;
+        T* yr = a.Y + (long long)(r0 + g) * ldy + c_lo;
         if (col_full)
           st_stream_vec<T, VEC>(yr, out);
         else
