@@ -267,7 +267,8 @@ int gbs_bcsr_destroy(gbs_bcsr* plan);
 /*
  * y <- A x  (Sec. 3).  vals, x and y have type `dtype`; x has n entries and
  * y has m entries.  The variant is chosen without looking at row_ptr
- * (merge-path, which balances any row-length distribution); its scratch
+ * (merge-path, which balances any row-length distribution: MERGE_DIRECT with
+ * 128 threads and 9 items per thread); its scratch
  * (one carry per CTA) comes from the stream-ordered allocator of the
  * current device (cudaMallocAsync / cudaFreeAsync on `stream`).  This
  * one-shot call never reads the row-length statistics, because reading them
@@ -298,8 +299,11 @@ int spmv_csr_cfg(int m, int n, int nnz, const int* row_ptr, const int* col_idx, 
  * about 20 bytes (FP64; 16 for FP32) per 3840 rows + nonzeros, so m + nnz up
  * to about 8.05e8 (FP64) or 1.0e9 (FP32) fits; larger sizes return
  * GBS_EUNSUPPORTED with a message (gbs_last_error) before anything is
- * launched.  Same dtypes, arguments,
- * results and determinism as spmv_csr; GBSPMV_CHECKED validation is not run.
+ * launched.  Same dtypes, arguments and determinism as spmv_csr; the
+ * product is the staged merge-path one (MERGE, 256 threads, 15 items per
+ * thread): bit for bit spmv_csr_cfg's result with that configuration, and
+ * within rounding of spmv_csr's own choice.  GBSPMV_CHECKED validation is
+ * not run.
  *
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it: make that first call before any

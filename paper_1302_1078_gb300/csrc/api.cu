@@ -627,9 +627,13 @@ static int product_entry(int m, int n, int nnz, const int* row_ptr, const int* c
   }
   gbs_config c{};
   if (cfg == nullptr || cfg->variant == GBS_VARIANT_AUTO) {
-    c.variant = GBS_VARIANT_MERGE;
-    c.threads = cfg && cfg->threads ? cfg->threads : 256;
-    c.items = cfg ? cfg->items : 0;
+    // merge-path, which needs no row statistics: SpMV with contiguous x and y takes the direct
+    // walk's SpMV form (128 threads x 9 items; 1.5-2x the staged form on the 27-point stencil,
+    // the banded matrix and R-MAT 22, scratch and partition included), SpMM the staged form
+    const bool spmv = k == 1 && ldx == 1 && ldy == 1;
+    c.variant = spmv ? GBS_VARIANT_MERGE_DIRECT : GBS_VARIANT_MERGE;
+    c.threads = cfg && cfg->threads ? cfg->threads : (spmv ? 128 : 256);
+    c.items = cfg && cfg->items ? cfg->items : (spmv ? 9 : 0);
     c.lanes = cfg ? cfg->lanes : 0;
     c.tile_nnz = 0;
   } else {

@@ -6,8 +6,8 @@ library.
 The test calls it through the C ABI on two calls in a row (different matrices, so the
 second call runs over the first call's leftover scratch) and checks each result
   * against the CPU oracle's y, within the parity bound the other tests use;
-  * bit for bit against spmv_csr, which runs the same merge-path configuration (256
-    threads, 15 items per thread, the same partition and carry fix-up) with scratch from
+  * bit for bit against spmv_csr_cfg with the same merge-path configuration (MERGE, 256
+    threads, 15 items per thread: the same partition and carry fix-up) and scratch from
     the stream-ordered allocator; a stale carry left in the shared array would show here;
 and checks that the two calls allocated nothing: the high-water mark of the device's
 default memory pool (where spmv_csr's scratch comes from) does not move, and neither does
@@ -85,8 +85,8 @@ def test_noalloc_matches_oracle_and_spmv_csr_on_two_calls(dtype):
         vh = M.vals.astype(NP[dtype])
         xh = synth.uniform(M.n, seed=9, stream=i).astype(NP[dtype])
         v, x = torch.from_numpy(vh).cuda(), torch.from_numpy(xh).cuda()
-        # spmv_csr's result first (it allocates its scratch from the pool), outside the window below
-        y_ref = gbs.spmv_csr(A["rp"], A["ci"], v, x)
+        # the stream-ordered result first (it allocates its scratch from the pool), outside the window below
+        y_ref = gbs.spmv_csr(A["rp"], A["ci"], v, x, config=dict(variant=2, threads=256, items=15))
         y = torch.full((M.m,), float("nan"), dtype=dtype, device="cuda")
         cases.append((M, A, vh, xh, v, x, y, y_ref))
     # the first call on a device looks up the static array's address, which loads the module that
@@ -119,7 +119,7 @@ def test_noalloc_matches_oracle_and_spmv_csr_on_two_calls(dtype):
         got = y.double().cpu().numpy()
         assert np.all(np.abs(got - y_orc) <= TOL[dtype] * r), f"call {i}: outside the bound of the oracle"
         assert np.all(got[r == 0] == 0.0)
-        assert torch.equal(y, y_ref), f"call {i}: not bitwise equal to spmv_csr's merge-path result"
+        assert torch.equal(y, y_ref), f"call {i}: not bitwise equal to the stream-ordered merge-path result"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
