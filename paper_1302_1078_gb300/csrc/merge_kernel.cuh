@@ -506,12 +506,65 @@ __device__ __forceinline__ void merge_fixup_one(int b, int ctas, int k, const in
   }
 }
 
+// The standalone fix-up: one thread per tile, as merge_fixup_one, except for runs longer than 8
+// tiles (a hub row; on R-MAT 22 one row spans 85 tiles), which the thread's warp takes over: the
+// run's end is found 32 tiles per step by a ballot, and its carries are loaded 32 at a time by
+// the lanes and added in tile order from shuffles.  The additions are merge_fixup_one's, in the
+// same order (so the batched kernel's fix-up gives the same bits); only the chain of dependent
+// loads is shortened.
 template <typename T>
 __global__ void merge_fixup_kernel(int ctas, int k, const int* __restrict__ carry_row, const T* __restrict__ carry_val,
                                    T* __restrict__ Y, long long ldy) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= ctas) return;
-  merge_fixup_one<T>(b, ctas, k, carry_row, carry_val, Y, ldy);
+  constexpr int W = 8;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int r = -1;
+  bool start = false;
+  if (b < ctas) {
+    r = __ldcg(carry_row + b);
+    start = r >= 0 && !(b > 0 && __ldcg(carry_row + b - 1) == r);
+  }
+  // a run of at most W tiles is summed by its own thread
+  bool longrun = false;
+  if (start) {
+    int rr[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) rr[j] = b + 1 + j < ctas ? __ldcg(carry_row + b + 1 + j) : -2;
+    bool ends = false;
+#pragma unroll
+    for (int j = 0; j < W; ++j) ends = ends || rr[j] != r;
+    if (ends)
+      merge_fixup_one<T>(b, ctas, k, carry_row, carry_val, Y, ldy);
+    else
+      longrun = true;
+  }
+  unsigned m = __ballot_sync(0xffffffffu, longrun);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const int rb = __shfl_sync(0xffffffffu, b, src), rr = __shfl_sync(0xffffffffu, r, src);
+    int re = ctas;  // the run is [rb, re)
+    for (int base = rb + 1; base < ctas; base += 32) {
+      const int t = base + lane;
+      const unsigned dm = __ballot_sync(0xffffffffu, t >= ctas || __ldcg(carry_row + t) != rr);
+      if (dm) {
+        re = base + __ffs(dm) - 1;
+        break;
+      }
+    }
+    for (int c = 0; c < k; ++c) {
+      Acc<T> acc;
+      for (int base = rb; base < re; base += 32) {
+        const T v = base + lane < re ? __ldcg(carry_val + (size_t)(base + lane) * k + c) : T(0);
+        const int cnt = min(32, re - base);
+        for (int j = 0; j < cnt; ++j) acc.add_partial(__shfl_sync(0xffffffffu, v, j));
+      }
+      if (lane == 0) {
+        T* yp = Y + (long long)rr * ldy + c;
+        *yp = __ldcg(yp) + acc.value();
+      }
+    }
+  }
 }
 
 }  // namespace gbs
