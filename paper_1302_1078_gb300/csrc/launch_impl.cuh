@@ -18,16 +18,16 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // The SM's 256 KB of unified storage is split between shared memory and L1.  Left to itself the
-// driver sizes the shared part for the 32 CTAs an SM can hold at most (64 KB for the direct merge
+// CUDA driver sizes the shared part for the 32 CTAs an SM can hold at most (64 KB for the direct merge
 // walk, which uses a few hundred bytes per CTA), and what it takes is lost to L1, where these
-// kernels' gathers of x hit.  The carveout attribute is only a hint, and the driver maps it to a
+// kernels' gathers of x hit.  The carveout attribute is only a hint, and the CUDA driver maps it to a
 // configuration in its own way; measured on GB300 (one probe kernel, ncu's
 // launch__shared_mem_config_size): hint 0 gives 8 KB, 1 gives 16 KB, 2 and 3 give 32 KB, 4 to 7
-// the default 64 KB, and the driver keeps the small ones even where they limit occupancy.
+// the default 64 KB, and the CUDA driver keeps the small ones even where they limit occupancy.
 // prefer_l1 therefore picks the smallest of 8, 16 and 32 KB that holds every CTA that can be
 // resident: an upper bound on that count from the thread, block and register limits (register
 // allocation rounded to 256 per warp), times the CTA's dynamic shared memory (rounded up to 256
-// bytes) plus the 1 KB the system reserves per CTA; above 32 KB it leaves the driver's default.
+// bytes) plus the 1 KB the system reserves per CTA; above 32 KB it leaves the CUDA driver's default.
 // The bound can only over-count, so the split never limits occupancy.  The device's limits are
 // read once per process (the library serves one kind of GPU); each kernel keeps its register
 // count and the hint it last set on which device, so a repeated launch makes no extra runtime call.
