@@ -844,8 +844,8 @@ std::vector<gbs_config> tune_candidates(const gbs_plan* p) {
     for (int it : {7, 9, 11, 13, 15, 23, 31, 47, 63}) add(GBS_VARIANT_MERGE_DIRECT, 0, 256, 0, it);
     // smaller CTAs: the direct walk is held to 40 registers, so twelve 128-thread (or twenty-four
     // 64-thread) CTAs fill an SM as six of 256 do, with finer tiles at the end of the grid
-    for (int it : {7, 9, 11, 13, 15}) add(GBS_VARIANT_MERGE_DIRECT, 0, 128, 0, it);
-    for (int it : {9, 11}) add(GBS_VARIANT_MERGE_DIRECT, 0, 64, 0, it);
+    for (int it : {7, 8, 9, 10, 11, 13, 15}) add(GBS_VARIANT_MERGE_DIRECT, 0, 128, 0, it);
+    for (int it : {8, 9, 10, 11}) add(GBS_VARIANT_MERGE_DIRECT, 0, 64, 0, it);
     for (int th : {128, 256}) add(GBS_VARIANT_ROWS_DIRECT, 1, th, 0, 0);
   } else {
     add(GBS_VARIANT_ROWS, 0, 256, base_tile, 0);

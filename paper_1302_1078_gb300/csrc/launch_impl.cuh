@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "launch.h"
 #include "merge_kernel.cuh"
@@ -33,20 +34,32 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 // count and the hint it last set on which device, so a repeated launch makes no extra runtime call.
 struct SmLimits {
   int reserved = 0, thr_sm = 0, blk_sm = 0, regs_sm = 0;
-  cudaError_t err = cudaSuccess;
 };
-static const SmLimits& sm_limits() {
-  static const SmLimits lim = [] {
+// The current device's limits, read once per process and kept only once they were read (a
+// failed query is returned and retried at the next launch).
+static cudaError_t sm_limits(SmLimits* out) {
+  static std::atomic<bool> ready{false};
+  static SmLimits cached;
+  static std::mutex mu;
+  if (ready.load(std::memory_order_acquire)) {
+    *out = cached;
+    return cudaSuccess;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ready.load(std::memory_order_relaxed)) {
     SmLimits l;
     int dev = 0;
-    l.err = cudaGetDevice(&dev);
-    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
-    if (l.err == cudaSuccess) l.err = cudaDeviceGetAttribute(&l.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    return l;
-  }();
-  return lim;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    cached = l;
+    ready.store(true, std::memory_order_release);
+  }
+  *out = cached;
+  return cudaSuccess;
 }
 
 struct L1Split {
@@ -56,10 +69,11 @@ struct L1Split {
 
 template <typename K>
 static cudaError_t prefer_l1(K kernel, int threads, size_t smem, L1Split& st) {
-  const SmLimits& l = sm_limits();
-  if (l.err != cudaSuccess) return l.err;
+  SmLimits l;
+  cudaError_t e = sm_limits(&l);
+  if (e != cudaSuccess) return e;
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   int r = st.regs.load(std::memory_order_relaxed);
   if (r <= 0) {
