@@ -159,3 +159,47 @@ def test_full_batch_512_k8(gbs):
     rng = np.random.default_rng(0)
     sample = sorted(set(rng.choice(len(specs), 24, replace=False).tolist()) | {0, 1, 2, 511})
     check_vs_oracle(host, batched, torch.float64, sample)
+
+
+def _hub_matrix():
+    """Empty rows around one 100k-nonzero row, a 7000-nonzero row and a few short ones."""
+    m, n = 64, 200000
+    lens = np.zeros(m, np.int64)
+    lens[5] = 100000
+    lens[6:12] = 3
+    lens[40] = 7000
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rng = np.random.default_rng(5)
+    ci = np.concatenate([np.sort(rng.choice(n, int(l), replace=False)) for l in lens if l > 0]).astype(np.int32)
+    return synth.CSR(m, n, rp.astype(np.int32), ci, rng.uniform(-1, 1, ci.size), "hub")
+
+
+@pytest.mark.parametrize("k,dtype", [(1, torch.float64), (4, torch.float64), (1, torch.float32)],
+                         ids=["k1f64", "k4f64", "k1f32"])
+def test_batched_hub_row_equals_looped(gbs, k, dtype):
+    """A row spanning about 56 merge tiles (256 threads x 7 items).  In the per-matrix loop the
+    standalone fix-up hands such a run of carries to a warp (loaded 32 at a time, added in tile
+    order); in the batched kernel the CTA that retires the matrix adds them one by one.  The two
+    must give the same bits, and both the oracle's result within the bound."""
+    mats, Xs, Ys, host = [], [], [], []
+    for i, A in enumerate([_hub_matrix(), synth.rmat(12, ef=8, seed=3)]):
+        rp = torch.from_numpy(A.row_ptr).cuda()
+        ci = torch.from_numpy(A.col_idx).cuda()
+        v = torch.from_numpy(A.vals.astype(NP[dtype])).cuda()
+        Xh = synth.uniform(A.n * k, seed=23, stream=i).astype(NP[dtype])
+        X = torch.from_numpy(Xh).cuda() if k == 1 else torch.from_numpy(Xh.reshape(A.n, k)).cuda()
+        Ys.append(torch.full((A.m,) if k == 1 else (A.m, k), float("nan"), dtype=dtype, device="cuda"))
+        mats.append((rp, ci, v, A.n))
+        Xs.append(X)
+        host.append((A, Xh.reshape(A.n, k)))
+    plan = gbs.BatchedPlan(mats, Xs, Ys, configs=[dict(variant=2, items=7), dict(variant=2, items=7)])
+    assert plan.info()["configs"][0]["variant"] == 2
+    plan.run()
+    torch.cuda.synchronize()
+    batched = [y.clone() for y in Ys]
+    check_vs_oracle(host, batched, dtype)
+    plan.run_looped()
+    torch.cuda.synchronize()
+    for b in range(len(Ys)):
+        assert torch.equal(Ys[b], batched[b]), f"batched != looped for matrix {b}"
